@@ -1,0 +1,421 @@
+"""Throughput of the laboratory-frame Glasma CPIC leapfrog step on GB300.
+
+Workload (default): the SU(3) single event, N_L = 512 x 64^2 transverse,
+dt = a/2, sigma_L = 8a, g^2 mu a = 0.1, m = 0.2/a, synthetic MV charges from
+a fixed seed; FP32 links and fields, FP64 reductions.  One bench step = one
+lattice time step of the whole event (CPIC hop on the scheduled steps,
+E update, link update).  Metric: site-updates/s (sites x steps / time).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W]
+                       [--impl ours|reference] [--precision fp32|fp64]
+Under torchrun (N > 1) every rank evolves its own event (replicas, no data
+exchange); value = all ranks' site-updates / max-over-ranks time.
+
+The reference arm (--impl reference) times the FP64 CPU oracle, as it
+stands, on the host cores: each step is one oracle step of a two-slice
+64 x 64 slab of the same SU(3) workload (a bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import glasma_inputs as gi  # noqa: E402
+
+WORKLOAD = "su3_512x64x64"
+METRIC = "site-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 comparison, e2e and error check")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# bytes per site-update of the step kernel (compulsory HBM traffic)
+# ---------------------------------------------------------------------------
+
+def bytes_per_site(nc, rs):
+    """Read and write the three links (SU(2): 4 reals, SU(3): 18 reals) and
+    the three E fields (nc^2 - 1 reals) of one site once."""
+    link = (4 if nc == 2 else 18) * rs
+    field = (nc * nc - 1) * rs
+    return 2 * 3 * (link + field)
+
+
+def step_kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2009_02044_gb300", "csrc")
+    for f in ("k_step.cu", "lattice.cuh", "su_n.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic(workload, precision):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu
+    summary, valid only if the kernel sources are unchanged since."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d[workload + ":" + precision]
+        if e["kernel_hash"] == step_kernel_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_state(cfg, nz, seed=0):
+    from oracle import glasma_oracle as O
+    p = O.Params.from_dict(dict(cfg, nz=nz))
+    rng = np.random.default_rng(seed)
+    nc, na = p.nc, p.na
+    U = gi.near_identity_su(nc, (3, nz, p.ny, p.nx), rng, 0.1)
+    U[2][nz - 1] = np.eye(nc)
+    E = 0.01 * rng.standard_normal((3, nz, p.ny, p.nx, na))
+    E[2][nz - 1] = 0.0
+    QA = np.zeros((nz, p.ny, p.nx, na))
+    QB = np.zeros((nz, p.ny, p.nx, na))
+    QB[0] = 0.01 * rng.standard_normal(QB[0].shape)
+    return O, O.State(p, U, E, QA, QB, 0)
+
+
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+        return int(n)
+    except Exception:
+        return 1
+
+
+def cpu_baseline(cfg, slices=16, steps=8):
+    O, st = oracle_sample_state(cfg, slices)
+    V = slices * cfg["nx"] * cfg["ny"]
+    t = time.perf_counter()
+    s = O.step(st, steps)
+    dt = time.perf_counter() - t
+    del s
+    return {"value": V * steps / dt, "unit": METRIC, "cores": 1,
+            "blas_threads": oracle_threads(), "kind": "oracle",
+            "sample": "%d FP64 oracle steps of a %d-slice %dx%d slab of the "
+                      "SU(3) workload (%d sites), %.1f s"
+                      % (steps, slices, cfg["nx"], cfg["ny"], V, dt)}
+
+
+def run_reference(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    slices = 2
+    O, st = oracle_sample_state(cfg, slices)
+    V = slices * cfg["nx"] * cfg["ny"]
+    for _ in range(args.warmup):
+        st = O.step(st, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        st = O.step(st, 1)
+    dt = time.perf_counter() - t
+    v = V * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SU(3) links/fields)",
+        "config": {"workload": args.workload, "sample": "%d-slice %dx%d slab"
+                   % (slices, cfg["nx"], cfg["ny"])},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1,
+                         "kind": "oracle",
+                         "sample": "one FP64 oracle step of a %d-slice "
+                                   "%dx%d slab (%d sites) per bench step"
+                                   % (slices, cfg["nx"], cfg["ny"], V)},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, cfg):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("gloo")
+    from paper_2009_02044_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2009_02044_gb300 import glasma as G
+
+    cfg = dict(cfg, precision=args.precision, seed=cfg["seed"] + rank)
+    stream = torch.cuda.Stream()
+    nc = cfg["nc"]
+    rs = 4 if args.precision == "fp32" else 8
+    V = cfg["nz"] * cfg["nx"] * cfg["ny"]
+    W, K = args.warmup, args.steps
+    if W < 3:
+        raise SystemExit("warmup must be >= 3")
+
+    with torch.cuda.stream(stream):
+        h = G.glasma_init_mv(cfg, None, stream=stream)
+    G.glasma_step(h, W)
+    info = G.glasma_get_info(h)
+    state_bytes = info.state_device_bytes
+    # count the hop launches in the timed window for the algorithmic bytes
+    from fractions import Fraction
+    r = Fraction(cfg["dt"]) / Fraction(cfg.get("a_z", 1.0))
+    pp, qq = r.numerator, r.denominator
+    hops = sum(1 for n in range(W, W + K)
+               if (2 * (n + 1) * pp + qq) // (2 * qq) > (2 * n * pp + qq) // (2 * qq))
+    na = nc * nc - 1
+    qbytes = 2 * rs * na * (info.window_a[1] + info.window_b[1]) * cfg["nx"] * cfg["ny"]
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        G.glasma_step(h, K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = G.glasma_get_info(h).kernel_launches
+    t = torch.tensor([ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * V * K / (ms_max * 1e-3)
+
+    # roofline of the step kernel (the only kernel in the timed region)
+    per_launch_ms = ms / launches
+    alg = V * bytes_per_site(nc, rs) + (hops / K) * qbytes
+    peak, peak_kind = load_peaks()
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    traffic = load_traffic(args.workload, args.precision)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "kernel": "k_step_leapfrog", "peak_source": peak_kind,
+            "alg_bytes_per_launch": alg}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(G, torch, cfg, args, stream, value)
+    gauss = G.glasma_gauss_residual(h)
+    G.glasma_free(h)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic (MV charges, seeded Philox)",
+            "config": {"workload": args.workload, "nc": nc,
+                       "lattice": [cfg["nz"], cfg["ny"], cfg["nx"]],
+                       "dt": cfg["dt"], "sigma_l": cfg["sigma_l"],
+                       "g2mu": cfg["g2mu"], "m_ir": cfg["m_ir"],
+                       "scheme": "leapfrog", "precision": args.precision,
+                       "reductions": "fp64",
+                       "l2": "inputs larger than L2 (state %.2f GB)"
+                             % (state_bytes / 1e9),
+                       "parallelism": "replicas" if world > 1 else "1 gpu"},
+            "roofline": roof,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "gauss_after": {"max": gauss[0], "rms": gauss[1],
+                            "rho_max": gauss[2]},
+        }
+        line.update(extras)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_extras(G, torch, cfg, args, stream, value):
+    """FP64 throughput, the FP32 energy-density error against the FP64 path
+    (itself parity-checked against the oracle), and the end-to-end number
+    through the C ABI from host buffers."""
+    out = {}
+    # end to end: host rho -> init -> K steps -> T^{mu nu} table to host
+    p = cfg
+    rho = gi.mv_rho(p["seed"], p["nc"], p["nx"], p["ny"], p["g2mu"])
+    rho_t = torch.from_numpy(rho).pin_memory()
+    rho_pinned = rho_t.numpy()
+    K = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        h = G.glasma_init_mv(p, rho_pinned, stream=stream)
+    G.glasma_step(h, K)
+    tab, H = G.glasma_tmunu(h)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    G.glasma_free(h)
+    V = p["nz"] * p["nx"] * p["ny"]
+    out["e2e"] = {"value": V * K / (t1 - t0), "unit": METRIC,
+                  "h2d_bytes_per_step": rho.nbytes / K,
+                  "d2h_bytes_per_step": tab.nbytes / K,
+                  "what": "glasma_init_mv from host rho + %d steps + "
+                          "glasma_tmunu to host, wall clock" % K}
+    # FP64 comparison run (same event) and energy-density error
+    other = "fp64" if args.precision == "fp32" else "fp32"
+    k64 = min(K, 400)
+    res = {}
+    for prec in (args.precision, other):
+        c = dict(p, precision=prec)
+        with torch.cuda.stream(stream):
+            hh = G.glasma_init_mv(c, rho_pinned, stream=stream)
+        tabs = []
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for blk in range(k64 // 50 + (1 if k64 % 50 else 0)):
+            n = min(50, k64 - 50 * blk)
+            ev0.record(stream)
+            G.glasma_step(hh, n)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            tot += ev0.elapsed_time(ev1)
+            tabs.append(G.glasma_tmunu(hh)[0][:, 0])
+        res[prec] = (V * k64 / (tot * 1e-3), np.array(tabs))
+        G.glasma_free(hh)
+    e32 = res["fp32"][1]
+    e64 = res["fp64"][1]
+    err = float(np.max(np.abs(e32 - e64)) / np.max(np.abs(e64)))
+    out["fp64"] = {"value": res["fp64"][0], "unit": METRIC, "steps": k64}
+    out["fp32_over_fp64"] = res["fp32"][0] / res["fp64"][0]
+    out["eps_error_fp32_vs_fp64"] = {
+        "max_rel": err, "definition":
+            "max over z and sampled t (every 50 steps) of |eps32 - eps64| / "
+            "max eps64; FP64 path parity-checked against the oracle"}
+    return out
+
+
+def main():
+    args = parse()
+    cfg = dict(gi.CONFIGS[args.workload])
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

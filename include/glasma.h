@@ -1,0 +1,227 @@
+/*
+ * glasma.h -- C ABI of the GB300 library for the laboratory-frame 3+1D Glasma
+ * time step with colored particle-in-cell (CPIC) charges.
+ *
+ * Method: D. Mueller and A. Ipp, "Progress on 3+1D Glasma simulations"
+ * (arXiv:2009.02044).  Section numbers and equation labels below refer to
+ * that paper.
+ *
+ * Units and conventions: lattice units with g = 1 and a_T = 1 by default;
+ * SU(N_c) generators t^a hermitian with tr(t^a t^b) = delta^{ab}/2;
+ * E_i = E_i^a t^a hermitian and U_i(t + dt) = exp(i dt E_i) U_i(t).
+ * Lattice: N_L = nz sites along the beam axis z (open boundary: there is no
+ * z link on the last slice) and nx * ny transverse sites (periodic).
+ * Nucleus A moves towards -z, nucleus B towards +z, both at v = c.
+ *
+ * Memory: a context owns every device buffer it uses.  It allocates them at
+ * glasma_init_mv through the optional allocator (or cudaMallocAsync on the
+ * given stream) and releases them in glasma_free.  All host pointers passed
+ * in are owned by the caller and only read or written during the call.
+ *
+ * Streams: a context is bound to one CUDA stream and one device.  Calls that
+ * return host values (residuals, tables, fields, state) synchronise that
+ * stream; glasma_step only enqueues work.
+ *
+ * Errors: every call returns GLASMA_OK (0) or a negative status; nothing is
+ * thrown across the ABI.  glasma_strerror(status) names the status, and
+ * glasma_last_error_message() gives the detail of the most recent failure
+ * on the calling thread.
+ */
+#ifndef GLASMA_H
+#define GLASMA_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define GLASMA_API __attribute__((visibility("default")))
+#else
+#define GLASMA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GLASMA_OK = 0,
+  GLASMA_ERR_INVALID_ARG = -1,   /* a parameter or size is out of range */
+  GLASMA_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  GLASMA_ERR_OOM = -3,           /* device allocation failed */
+  GLASMA_ERR_NONFINITE = -4,     /* a reduction met NaN or Inf */
+  GLASMA_ERR_PARTICLE_EXIT = -5, /* a charge would leave the open z range */
+  GLASMA_ERR_NOT_CONVERGED = -6, /* implicit iteration hit max_iter */
+  GLASMA_ERR_TIMEOUT = -7,       /* a bounded device wait expired */
+  GLASMA_ERR_CHECKSUM = -8,      /* a state blob failed its checksum */
+  GLASMA_ERR_INTERNAL = -9       /* an internal consistency check failed */
+};
+
+enum { GLASMA_FP64 = 0, GLASMA_FP32 = 1 };
+enum { GLASMA_LEAPFROG = 0, GLASMA_IMPLICIT = 1 };
+
+typedef struct glasma_ctx glasma_ctx;
+
+/* Parameters of one event (Sec. 3 and 4).  Sizes in units of a_t. */
+typedef struct {
+  int nc;                   /* gauge group SU(nc): 2 or 3 */
+  int nz, nx, ny;           /* N_L (beam axis, open) and transverse sizes */
+  double a_t, a_z, dt;      /* transverse and longitudinal spacing, time step */
+  double sigma_l;           /* std. dev. of the Gaussian longitudinal profile */
+  double g2mu;              /* g^2 mu a_t: std. dev. of rho^a per cell */
+  double m_ir;              /* infrared regulator m of the Poisson solve */
+  double uv_cutoff;         /* UV cutoff Lambda on k_T; 0 = none */
+  double z_offset;          /* initial distance of each nucleus from the box
+                               centre; 0 = (ceil(4 sigma_l / a_z) + 2) a_z */
+  unsigned long long seed;  /* MV charge seed (used when rho is not given) */
+  int precision;            /* GLASMA_FP64 or GLASMA_FP32 (FP32 links and
+                               fields; every reduction in FP64) */
+  int scheme;               /* GLASMA_LEAPFROG or GLASMA_IMPLICIT */
+  int implicit_max_iter;    /* fixed-point iterations of the implicit scheme */
+  double implicit_tol;      /* its convergence threshold on max |dE| */
+} glasma_params;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Both
+ * callbacks are called only from glasma_init_mv / glasma_free /
+ * glasma_set_fields on the calling thread. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} glasma_allocator;
+
+/*
+ * Build the MV initial state at t0 (links) and t0 - dt/2 (E and charges)
+ * (Sec. 2 MV model; Sec. 3 Eqs. single_sheet, 3d_colorfield_1/2; Sec. 4
+ * Gaussian longitudinal profile):
+ *   rho_N^a(x_T) -> phi_N = (-Delta_T + m^2)^{-1} rho_N (lattice Laplacian,
+ *   optional UV cutoff) -> V_N^dagger(z, x_T) = exp(i Lambda_N(z) phi_N)
+ *   -> U_i = V_A(x) V_A^dag(x+i) V_B(x) V_B^dag(x+i) for i = x, y, U_z = 1,
+ *   at t0 and t0 - dt; E = -i log(U(t0) U^dag(t0 - dt)) / dt (0 where the
+ *   two links are equal); charges from the discrete Gauss law (Eq. gauss),
+ *   split by the side of the box centre into the two nuclei.
+ * p:        parameters (read only).
+ * rho_host: NULL to draw rho from p->seed (Philox4x32-10, counter
+ *           (x, y, a, N), Box-Muller), or host doubles [2][nc^2-1][ny][nx]
+ *           (N = 0: A, N = 1: B) in units of a_t^-2.
+ * stream:   cudaStream_t the context will use (NULL = legacy default).
+ * alloc:    NULL for cudaMallocAsync, else the callbacks above.
+ * out:      receives the new context (NULL on failure).
+ * Errors: INVALID_ARG (nc, sizes, dt > a_z, dt/a_z not a ratio p/q with
+ * q <= 4096, nuclei not inside the box), OOM, CUDA, INTERNAL.
+ */
+GLASMA_API int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
+                   const glasma_allocator* alloc, glasma_ctx** out);
+
+/*
+ * Advance n_steps time steps (n_steps >= 0).  Each step (Sec. 3):
+ * (1) if the nearest-grid-point position of the charges changes (hop
+ *     counter floor(m v dt / a_z + 1/2)), each charge is parallel
+ *     transported along the crossed z link, Q' = U^dag Q U, and the current
+ *     that satisfies the discrete continuity equation (Eq. continuity) is
+ *     deposited on that link;
+ * (2) E_i += -dt sum_j (2/a_j^2) Im tr t^a [U_{i,j} + U_{i,-j}] + dt j_i
+ *     (Eq. lattice_1 with Eq. plaquette);
+ * (3) U_i <- exp(i dt E_i) U_i (Eq. lattice_2), re-unitarised in FP32.
+ * With scheme = GLASMA_IMPLICIT step (2) uses the time-averaged transverse
+ * terms of the semi-implicit scheme (Sec. 3, Fig. wilson (b)), iterated.
+ * Enqueued on the context's stream; returns before the work completes.
+ * Errors: PARTICLE_EXIT (checked on the host before any work of the
+ * offending step is enqueued), NOT_CONVERGED, CUDA, INVALID_ARG.
+ */
+GLASMA_API int glasma_step(glasma_ctx* c, int n_steps);
+
+/*
+ * Discrete Gauss law (Sec. 3, Eq. gauss) with parallel-transported E:
+ *   G^a(x) = sum_i [E_i(x) - U_i^dag(x-i) E_i(x-i) U_i(x-i)]^a / a_i^2
+ *            - rho^a(x),  rho = Q_A + Q_B,
+ * evaluated in FP64 for either precision (at z = 0 no link enters from
+ * below).  Outputs (host doubles, any may be NULL): max_{x,a} |G|, the rms
+ * of G over all components, and max |rho|.  Synchronises the stream.
+ * Errors: NONFINITE, CUDA.
+ */
+GLASMA_API int glasma_gauss_residual(glasma_ctx* c, double* max_abs, double* rms, double* rho_max);
+
+/*
+ * Energy-momentum tensor per z slice at t_n (Sec. 4: eps, p_L, p_T, S_L of
+ * <T^{mu nu}>; Eq. pT_eL), transverse means accumulated in FP64:
+ *   e_i^2 = (1/2) sum_a [E_i^a(n-1/2)^2 + E_i^a(n+1/2)^2] / a_i^2,
+ *   b_ij = 2 (N_c - Re tr U_ij) / (a_i a_j)^2 at the plaquette's base,
+ *   eps = (e_x^2+e_y^2+e_z^2)/2 + b_xy + b_xz + b_yz,
+ *   p_T = e_z^2/2 + b_xy,  p_L = eps - 2 p_T,
+ *   S_L = sum_a (Ebar_x B_y - Ebar_y B_x) (physical Poynting flux,
+ *   positive towards +z), Ebar = time mean of E / a_i,
+ *   B_k = -2 Im tr(t^a U_ij) / (a_i a_j) for cyclic (i, j, k).
+ * E(n+1/2) comes from a non-committing evaluation of the next E update
+ * (including the current of a scheduled hop); the state is unchanged.
+ * out: host doubles [nz][4] = (eps, p_L, p_T, S_L) per slice, or NULL.
+ * energy_total: a_t^2 a_z nx ny sum_z eps(z), or NULL.
+ * Synchronises the stream.  Errors: NONFINITE, CUDA.
+ */
+GLASMA_API int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total);
+
+/* Release every device buffer of the context (stream-ordered) and the
+ * context itself.  NULL is ignored. */
+GLASMA_API void glasma_free(glasma_ctx* c);
+
+/* Static string naming a status code. */
+GLASMA_API const char* glasma_strerror(int status);
+
+/* Detail of the most recent failure on this thread (static storage). */
+GLASMA_API const char* glasma_last_error_message(void);
+
+/*
+ * Fields in FP64, full lattice, for analysis and tests.  Any pointer may be
+ * NULL.  Layouts (host doubles, x fastest):
+ *   U  [3][nz][ny][nx][nc][nc][2]  (complex matrices, re/im interleaved)
+ *   E  [3][nz][ny][nx][nc^2-1]
+ *   QA, QB [nz][ny][nx][nc^2-1]    (charges placed at their lattice sites)
+ * step_n receives the step index n (U at t_n, E and charges at t_{n-1/2}).
+ * Synchronises the stream.
+ */
+GLASMA_API int glasma_get_fields(glasma_ctx* c, double* U, double* E, double* QA, double* QB,
+                      long long* step_n);
+
+/*
+ * Replace the state by host FP64 fields in the layouts of glasma_get_fields
+ * (U, E required; QA, QB may be NULL for zero charges) at step index
+ * step_n.  Values are rounded to the context's precision.  The z link of
+ * the last slice must be the identity and E_z there zero.  The charge
+ * windows are rebuilt from the nonzero slices of QA and QB.  U_prev (the
+ * links at t_{n-1}, used by the implicit scheme) may be NULL, in which case
+ * exp(-i dt E) U is used.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+GLASMA_API int glasma_set_fields(glasma_ctx* c, const double* U, const double* E, const double* QA,
+                      const double* QB, const double* U_prev, long long step_n);
+
+/* Size in bytes of the checkpoint blob of glasma_get_state. */
+GLASMA_API int glasma_state_bytes(const glasma_ctx* c, size_t* bytes);
+
+/*
+ * Checkpoint: the state (links, E, charge windows, step index, parameters)
+ * in the context's own precision, with a header and a CRC-32 per array, so
+ * that glasma_set_state restores a bitwise identical state.
+ * Errors: INVALID_ARG (buffer too small or from another configuration),
+ * CHECKSUM, CUDA.
+ */
+GLASMA_API int glasma_get_state(glasma_ctx* c, void* host_buf, size_t bytes);
+GLASMA_API int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes);
+
+/* Introspection for benchmarks: sites, bytes per link/field and device
+ * pointers of the current buffers.  Any pointer may be NULL. */
+typedef struct {
+  long long sites;          /* nz * ny * nx */
+  long long step_n;         /* current step index */
+  int nc, precision, scheme;
+  int window_a[2];          /* charge window of A: first slice, slices */
+  int window_b[2];          /* charge window of B */
+  size_t state_device_bytes; /* device bytes of U (both buffers), E, charges */
+  int kernel_launches;      /* kernels enqueued by the last glasma_step call */
+  int implicit_iters;       /* fixed-point iterations of the last implicit step */
+} glasma_info;
+
+GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLASMA_H */

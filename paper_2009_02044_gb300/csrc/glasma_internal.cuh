@@ -1,0 +1,72 @@
+// Context object behind the C ABI and the host-side launchers of each kernel
+// family.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/glasma.h"
+#include "lattice.cuh"
+
+struct glasma_ctx {
+  glasma_params p;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  glasma_allocator alloc{};
+  bool has_alloc = false;
+  int na = 0, nv = 0;
+  glasma::Geom g{};
+  size_t rs = 8;              // bytes per real of the state
+  void* U[2] = {nullptr, nullptr};
+  int cur = 0;                // U[cur] holds U(t_n)
+  void* Uprev = nullptr;      // U(t_{n-1}), implicit scheme only
+  void* E = nullptr;          // E(t_{n-1/2})
+  void* Ework = nullptr;      // implicit scheme: E(t_{n-1/2}) kept during iteration
+  void* QA = nullptr;         // charge windows (co-moving slots)
+  void* QB = nullptr;
+  int zA0 = 0, WA = 0, zB0 = 0, WB = 0;  // first slice and slices of each window
+  size_t QA_cap = 0, QB_cap = 0;        // allocated slots
+  long long n = 0;
+  long long hop_p = 1, hop_q = 2;       // v dt / a_z = p / q
+  double* red = nullptr;      // reduction partials
+  size_t red_cap = 0;         // doubles
+  double* tab = nullptr;      // [nz][4] T^{mu nu} table
+  int* dflag = nullptr;       // device status word(s)
+  int last_launches = 0;
+  int last_iters = 0;
+  struct Alloc {
+    void* ptr;
+    size_t bytes;
+  };
+  std::vector<Alloc> allocs;
+};
+
+namespace glasma {
+
+// status helpers (defined in glasma_api.cu)
+int set_error(int status, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+void* ctx_alloc(glasma_ctx* c, size_t bytes);
+void ctx_free(glasma_ctx* c, void* p);
+
+// number of hops after m steps: floor(m p/q + 1/2) in integers
+inline long long hop_count(long long m, long long p, long long q) {
+  return (2 * m * p + q) / (2 * q);
+}
+inline bool hop_at(long long n, long long p, long long q) {
+  return hop_count(n + 1, p, q) > hop_count(n, p, q);
+}
+
+// kernel launchers
+int launch_step_leapfrog(glasma_ctx* c, bool hop);
+int launch_step_implicit(glasma_ctx* c, bool hop, int* iters);
+int launch_gauss(glasma_ctx* c, double* out3);
+int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab);
+int run_init(glasma_ctx* c, const double* rho_host);
+
+// checkpoint CRC-32 (IEEE 802.3 polynomial, reflected)
+uint32_t crc32(const void* data, size_t n, uint32_t crc = 0);
+
+}  // namespace glasma

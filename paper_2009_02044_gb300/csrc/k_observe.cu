@@ -1,0 +1,339 @@
+// Observables with FP64 accumulation: the discrete Gauss law residual
+// (Sec. 3, Eq. gauss) and the per-slice energy-momentum tensor (Sec. 4).
+// Reductions are deterministic: fixed grid, fixed-order tree in shared
+// memory, fixed-order final pass over the block partials.
+#include "glasma_internal.cuh"
+
+namespace glasma {
+
+constexpr int kRedThreads = 256;
+
+// In-block tree reduction of NV doubles per thread; op 0 = sum, 1 = max.
+template <int NV>
+__device__ void block_reduce(double (*sh)[kRedThreads], double* v, const int* op) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sh[k][t] = v[k];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (t < w) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        sh[k][t] = op[k] ? fmax(sh[k][t], sh[k][t + w]) : sh[k][t] + sh[k][t + w];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = sh[k][0];
+}
+
+// ---------------------------------------------------------------------------
+// Gauss residual
+// ---------------------------------------------------------------------------
+template <typename R>
+struct GaussArgs {
+  const typename V2T<R>::T* U;
+  const R* E;
+  const R* QA;
+  const R* QB;
+  Geom g;
+  double ia2[3];  // 1 / a_i^2
+  int zA0, WA, zB0, WB;
+  double* part;  // [gridDim][4]
+};
+
+template <int NC, typename R>
+__global__ void __launch_bounds__(kRedThreads) k_gauss(GaussArgs<R> a) {
+  typedef Group<NC, double> G;
+  constexpr int NA = G::NA;
+  __shared__ double sh[4][kRedThreads];
+  double gmax = 0, gsum2 = 0, rmax = 0, bad = 0;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.g.V;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    SiteNbr n = site_nbr(a.g, s);
+    double gv[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) gv[c] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double q[NA];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) gv[c] += a.ia2[i] * (double)a.E[(int64_t)(i * NA + c) * a.g.V + s];
+      if (i == 2 && n.iz == 0) continue;
+      const int64_t sm = n.m[i];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) q[c] = (double)a.E[(int64_t)(i * NA + c) * a.g.V + sm];
+      typename G::M um = LinkIO<NC, R>::template load<double>(a.U, i, a.g.V, sm);
+      G::adj_dag(um, q);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) gv[c] -= a.ia2[i] * q[c];
+    }
+    const int64_t t = s % a.g.nxy;
+    double rho[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) rho[c] = 0.0;
+    const int ka = n.iz - a.zA0, kb = n.iz - a.zB0;
+    if (ka >= 0 && ka < a.WA)
+#pragma unroll
+      for (int c = 0; c < NA; ++c) rho[c] += (double)a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
+    if (kb >= 0 && kb < a.WB)
+#pragma unroll
+      for (int c = 0; c < NA; ++c) rho[c] += (double)a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) {
+      double r = gv[c] - rho[c];
+      if (!isfinite(r)) bad += 1.0;
+      gmax = fmax(gmax, fabs(r));
+      gsum2 += r * r;
+      rmax = fmax(rmax, fabs(rho[c]));
+    }
+  }
+  double v[4] = {gmax, gsum2, rmax, bad};
+  const int op[4] = {1, 0, 1, 0};
+  block_reduce<4>(sh, v, op);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.part[blockIdx.x * 4 + k] = v[k];
+}
+
+// One block folds nb partials of width NV in a fixed order; bit k of MAXMASK
+// selects max (else sum) for component k.
+template <int NV, int MAXMASK>
+__global__ void __launch_bounds__(kRedThreads) k_fold(const double* part, int nb, double* out) {
+  __shared__ double sh[NV][kRedThreads];
+  int op[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) op[k] = (MAXMASK >> k) & 1;
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kRedThreads)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = op[k] ? fmax(v[k], part[b * NV + k]) : v[k] + part[b * NV + k];
+  block_reduce<NV>(sh, v, op);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = v[k];
+}
+
+static int reduction_grid(glasma_ctx* c) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  int64_t need = (c->g.V + kRedThreads - 1) / kRedThreads;
+  int64_t nb = (int64_t)sms * 4;
+  return (int)(need < nb ? need : nb);
+}
+
+template <int NC, typename R>
+static int gauss_t(glasma_ctx* c, double* out3) {
+  GaussArgs<R> a;
+  a.U = (const typename V2T<R>::T*)c->U[c->cur];
+  a.E = (const R*)c->E;
+  a.QA = (const R*)c->QA;
+  a.QB = (const R*)c->QB;
+  a.g = c->g;
+  a.ia2[0] = a.ia2[1] = 1.0 / (c->p.a_t * c->p.a_t);
+  a.ia2[2] = 1.0 / (c->p.a_z * c->p.a_z);
+  a.zA0 = c->zA0;
+  a.WA = c->WA;
+  a.zB0 = c->zB0;
+  a.WB = c->WB;
+  const int nb = reduction_grid(c);
+  // partials, then the op table and the 4 results, in the context's scratch
+  if ((size_t)nb * 4 + 8 > c->red_cap) return set_error(GLASMA_ERR_INTERNAL, "reduction scratch too small");
+  a.part = c->red;
+  double* res = c->red + (size_t)nb * 4;
+  k_gauss<NC, R><<<nb, kRedThreads, 0, c->stream>>>(a);
+  int st = cuda_check(cudaGetLastError(), "k_gauss launch");
+  if (st) return st;
+  k_fold<4, 0x5><<<1, kRedThreads, 0, c->stream>>>(c->red, nb, res);
+  st = cuda_check(cudaGetLastError(), "k_fold launch");
+  if (st) return st;
+  double h[4];
+  st = cuda_check(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "gauss readback");
+  if (st) return st;
+  st = cuda_check(cudaStreamSynchronize(c->stream), "gauss sync");
+  if (st) return st;
+  out3[0] = h[0];
+  out3[1] = sqrt(h[1] / ((double)c->g.V * (c->na)));
+  out3[2] = h[2];
+  if (h[3] != 0.0) return set_error(GLASMA_ERR_NONFINITE, "Gauss residual met a non-finite value");
+  return GLASMA_OK;
+}
+
+int launch_gauss(glasma_ctx* c, double* out3) {
+  if (c->p.nc == 2) return c->rs == 8 ? gauss_t<2, double>(c, out3) : gauss_t<2, float>(c, out3);
+  return c->rs == 8 ? gauss_t<3, double>(c, out3) : gauss_t<3, float>(c, out3);
+}
+
+// ---------------------------------------------------------------------------
+// T^{mu nu} per z slice
+// ---------------------------------------------------------------------------
+template <typename R>
+struct TmnArgs {
+  const typename V2T<R>::T* U;
+  const R* E;
+  const R* QA;
+  const R* QB;
+  Geom g;
+  R dt;
+  R w[3];
+  R az2;
+  double a[3];
+  int hop;
+  int zA0, WA, zB0, WB;
+  double* tab;  // [nz][4]
+};
+
+// Per-site arithmetic in the state's precision R (so E(n+1/2) equals what
+// the step kernel would write), every accumulation in FP64.
+template <int NC, typename R>
+__global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
+  typedef Group<NC, R> G;
+  typedef typename G::M M;
+  constexpr int NA = G::NA;
+  __shared__ double sh[5][kRedThreads];
+  const int iz = blockIdx.x;
+  double eps = 0, pl = 0, pt = 0, sl = 0, bad = 0;
+  for (int t = threadIdx.x; t < a.g.nxy; t += blockDim.x) {
+    const int64_t s = (int64_t)iz * a.g.nxy + t;
+    SiteNbr n = site_nbr(a.g, s);
+    M Uo[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Uo[d] = LinkIO<NC, R>::template load<R>(a.U, d, a.g.V, s);
+    double e2[3] = {0, 0, 0};
+    double eb[2][NA];
+    const int ilast = (iz == a.g.nz - 1) ? 2 : 3;
+    for (int i = 0; i < ilast; ++i) {
+      R F[NA];
+      link_force<NC, R, R>(a.U, a.g, n, Uo, i, a.w, F);
+      R en[NA], eo[NA];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) {
+        eo[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
+        en[c] = eo[c] + a.dt * F[c];
+      }
+      if (i == 2 && a.hop) {
+        R dj[NA];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) dj[c] = R(0);
+        const int kb = iz - a.zB0;
+        if (kb >= 0 && kb < a.WB)
+#pragma unroll
+          for (int c = 0; c < NA; ++c) dj[c] -= a.az2 * a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
+        const int ka = iz + 1 - a.zA0;
+        if (ka >= 0 && ka < a.WA) {
+          R q[NA];
+#pragma unroll
+          for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
+          G::adj(Uo[2], q);
+#pragma unroll
+          for (int c = 0; c < NA; ++c) dj[c] += a.az2 * q[c];
+        }
+#pragma unroll
+        for (int c = 0; c < NA; ++c) en[c] += dj[c];
+      }
+      double acc = 0;
+#pragma unroll
+      for (int c = 0; c < NA; ++c) {
+        double o = (double)eo[c], nn = (double)en[c];
+        acc += o * o + nn * nn;
+        if (i < 2) eb[i][c] = 0.5 * (o + nn) / a.a[i];
+      }
+      e2[i] = 0.5 * acc / (a.a[i] * a.a[i]);
+    }
+    // magnetic terms from the plaquettes at the base site, in FP64:
+    // b_ij = ||U_i(x) U_j(x+i) - U_j(x) U_i(x+j)||_F^2 / (a_i a_j)^2
+    // (= 2 (N - Re tr U_ij) for unitary links, without its cancellation),
+    // B from Im tr t^a U_ij with U_ij = A B^dagger
+    typedef Group<NC, double> GD;
+    typedef typename GD::M MD;
+    MD ud[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ud[d] = LinkIO<NC, R>::template load<double>(a.U, d, a.g.V, s);
+    double bxy, bxz = 0, byz = 0;
+    double Bx[NA], By[NA];
+    {
+      MD A = GD::mul(ud[0], LinkIO<NC, R>::template load<double>(a.U, 1, a.g.V, n.p[0]));
+      MD B = GD::mul(ud[1], LinkIO<NC, R>::template load<double>(a.U, 0, a.g.V, n.p[1]));
+      bxy = GD::fro2_diff(A, B) / (a.a[0] * a.a[1] * a.a[0] * a.a[1]);
+    }
+#pragma unroll
+    for (int c = 0; c < NA; ++c) Bx[c] = By[c] = 0.0;
+    if (iz <= a.g.nz - 2) {
+      double pr[NA];
+      MD A = GD::mul(ud[0], LinkIO<NC, R>::template load<double>(a.U, 2, a.g.V, n.p[0]));  // U_x U_z(x+x)
+      MD B = GD::mul(ud[2], LinkIO<NC, R>::template load<double>(a.U, 0, a.g.V, n.p[2]));  // U_z U_x(x+z)
+      bxz = GD::fro2_diff(A, B) / (a.a[0] * a.a[2] * a.a[0] * a.a[2]);
+      GD::proj(GD::mul_d(A, B), pr);  // B_y = -2 Im tr t U_zx / (a_z a_x) = +2 Im tr t U_xz / (a_x a_z)
+#pragma unroll
+      for (int c = 0; c < NA; ++c) By[c] = 2.0 * pr[c] / (a.a[0] * a.a[2]);
+      A = GD::mul(ud[1], LinkIO<NC, R>::template load<double>(a.U, 2, a.g.V, n.p[1]));  // U_y U_z(x+y)
+      B = GD::mul(ud[2], LinkIO<NC, R>::template load<double>(a.U, 1, a.g.V, n.p[2]));  // U_z U_y(x+z)
+      byz = GD::fro2_diff(A, B) / (a.a[1] * a.a[2] * a.a[1] * a.a[2]);
+      GD::proj(GD::mul_d(A, B), pr);  // B_x = -2 Im tr t U_yz / (a_y a_z)
+#pragma unroll
+      for (int c = 0; c < NA; ++c) Bx[c] = -2.0 * pr[c] / (a.a[1] * a.a[2]);
+    }
+    double s_l = 0;
+#pragma unroll
+    for (int c = 0; c < NA; ++c) s_l += eb[0][c] * By[c] - eb[1][c] * Bx[c];
+    double e = 0.5 * (e2[0] + e2[1] + e2[2]) + bxy + bxz + byz;
+    double p_t = 0.5 * e2[2] + bxy;
+    double p_l = 0.5 * (e2[0] + e2[1]) + bxz + byz - p_t;
+    if (!isfinite(e) || !isfinite(s_l)) bad += 1.0;
+    eps += e;
+    pl += p_l;
+    pt += p_t;
+    sl += s_l;
+  }
+  double v[5] = {eps, pl, pt, sl, bad};
+  const int op[5] = {0, 0, 0, 0, 0};
+  block_reduce<5>(sh, v, op);
+  if (threadIdx.x == 0) {
+    const double inv = 1.0 / (double)a.g.nxy;
+    a.tab[iz * 4 + 0] = v[0] * inv;
+    a.tab[iz * 4 + 1] = v[1] * inv;
+    a.tab[iz * 4 + 2] = v[2] * inv;
+    a.tab[iz * 4 + 3] = v[3] * inv;
+    if (v[4] != 0.0) a.tab[iz * 4 + 0] = __longlong_as_double(0x7ff8000000000000LL);  // NaN marks it
+  }
+}
+
+template <int NC, typename R>
+static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab) {
+  TmnArgs<R> a;
+  a.U = (const typename V2T<R>::T*)c->U[c->cur];
+  a.E = (const R*)c->E;
+  a.QA = (const R*)c->QA;
+  a.QB = (const R*)c->QB;
+  a.g = c->g;
+  a.dt = (R)c->p.dt;
+  a.w[0] = (R)(2.0 / (c->p.a_t * c->p.a_t));
+  a.w[1] = a.w[0];
+  a.w[2] = (R)(2.0 / (c->p.a_z * c->p.a_z));
+  a.az2 = (R)(c->p.a_z * c->p.a_z);
+  a.a[0] = a.a[1] = c->p.a_t;
+  a.a[2] = c->p.a_z;
+  a.hop = hop ? 1 : 0;
+  a.zA0 = c->zA0;
+  a.WA = c->WA;
+  a.zB0 = c->zB0;
+  a.WB = c->WB;
+  a.tab = c->tab;
+  k_tmunu<NC, R><<<c->g.nz, kRedThreads, 0, c->stream>>>(a);
+  int st = cuda_check(cudaGetLastError(), "k_tmunu launch");
+  if (st) return st;
+  st = cuda_check(cudaMemcpyAsync(host_tab, c->tab, sizeof(double) * 4 * c->g.nz, cudaMemcpyDeviceToHost,
+                                  c->stream),
+                  "tmunu readback");
+  if (st) return st;
+  return cuda_check(cudaStreamSynchronize(c->stream), "tmunu sync");
+}
+
+int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab) {
+  if (c->p.nc == 2) return c->rs == 8 ? tmunu_t<2, double>(c, hop, host_tab) : tmunu_t<2, float>(c, hop, host_tab);
+  return c->rs == 8 ? tmunu_t<3, double>(c, hop, host_tab) : tmunu_t<3, float>(c, hop, host_tab);
+}
+
+}  // namespace glasma

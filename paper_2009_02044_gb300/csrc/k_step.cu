@@ -1,0 +1,121 @@
+// Fused leapfrog step with the CPIC hop (Sec. 3, Eqs. lattice_1, lattice_2,
+// continuity and the NGP parallel transport).
+//
+// One thread per site.  For each of the site's three links it
+//   (1) on a hop step and for the z link: transports the charge of B that
+//       sits at x to x+z (Q' = U_z^dag Q U_z) and the charge of A that sits
+//       at x+z to x (Q' = U_z Q U_z^dag), and deposits dt J_z =
+//       a_z^2 (Q'_A - Q_B) (the current that satisfies the continuity
+//       equation with Gauss weights 1/a_i^2);
+//   (2) adds dt times the plaquette force to E;
+//   (3) writes exp(i dt E) U to the other link buffer (re-unitarised in FP32).
+// The charges live in co-moving windows: a hop rewrites each slot in place
+// and the host moves the window origin by one slice afterwards, so no slot
+// is touched by two threads.
+#include "glasma_internal.cuh"
+
+namespace glasma {
+
+template <typename R>
+struct StepArgs {
+  const typename V2T<R>::T* U;
+  typename V2T<R>::T* Un;
+  R* E;
+  R* QA;
+  R* QB;
+  Geom g;
+  R dt;
+  R w[3];   // 2 / a_j^2
+  R az2;    // a_z^2
+  int hop;
+  int zA0, WA, zB0, WB;
+};
+
+template <int NC, typename R>
+__global__ void __launch_bounds__(128) k_step_leapfrog(StepArgs<R> a) {
+  typedef Group<NC, R> G;
+  typedef typename G::M M;
+  constexpr int NA = G::NA;
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.g.V) return;
+  SiteNbr n = site_nbr(a.g, s);
+  M Uo[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Uo[d] = LinkIO<NC, R>::template load<R>(a.U, d, a.g.V, s);
+  const int ilast = (n.iz == a.g.nz - 1) ? 2 : 3;  // no z link on the last slice
+  for (int i = 0; i < ilast; ++i) {
+    R F[NA];
+    link_force<NC, R, R>(a.U, a.g, n, Uo, i, a.w, F);
+    R e[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s] + a.dt * F[c];
+    if (i == 2 && a.hop) {
+      const int64_t t = s % a.g.nxy;
+      R dj[NA];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) dj[c] = R(0);
+      const int kb = n.iz - a.zB0;
+      if (kb >= 0 && kb < a.WB) {
+        R q[NA];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) q[c] = a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) dj[c] -= a.az2 * q[c];
+        G::adj_dag(Uo[2], q);
+#pragma unroll
+        for (int c = 0; c < NA; ++c) a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t] = q[c];
+      }
+      const int ka = n.iz + 1 - a.zA0;
+      if (ka >= 0 && ka < a.WA) {
+        R q[NA];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
+        G::adj(Uo[2], q);
+#pragma unroll
+        for (int c = 0; c < NA; ++c) {
+          dj[c] += a.az2 * q[c];
+          a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t] = q[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NA; ++c) e[c] += dj[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NA; ++c) a.E[(int64_t)(i * NA + c) * a.g.V + s] = e[c];
+    M un = G::mul(G::expi(e, a.dt), Uo[i]);
+    if (sizeof(R) == 4) un = G::reunit(un);
+    LinkIO<NC, R>::template store<R>(a.Un, i, a.g.V, s, un);
+  }
+}
+
+template <int NC, typename R>
+static int launch_t(glasma_ctx* c, bool hop) {
+  StepArgs<R> a;
+  a.U = (const typename V2T<R>::T*)c->U[c->cur];
+  a.Un = (typename V2T<R>::T*)c->U[1 - c->cur];
+  a.E = (R*)c->E;
+  a.QA = (R*)c->QA;
+  a.QB = (R*)c->QB;
+  a.g = c->g;
+  a.dt = (R)c->p.dt;
+  a.w[0] = (R)(2.0 / (c->p.a_t * c->p.a_t));
+  a.w[1] = a.w[0];
+  a.w[2] = (R)(2.0 / (c->p.a_z * c->p.a_z));
+  a.az2 = (R)(c->p.a_z * c->p.a_z);
+  a.hop = hop ? 1 : 0;
+  a.zA0 = c->zA0;
+  a.WA = c->WA;
+  a.zB0 = c->zB0;
+  a.WB = c->WB;
+  const int bs = 128;
+  const int64_t nb = (c->g.V + bs - 1) / bs;
+  k_step_leapfrog<NC, R><<<(unsigned)nb, bs, 0, c->stream>>>(a);
+  return cuda_check(cudaGetLastError(), "k_step_leapfrog launch");
+}
+
+int launch_step_leapfrog(glasma_ctx* c, bool hop) {
+  if (c->p.nc == 2) return c->rs == 8 ? launch_t<2, double>(c, hop) : launch_t<2, float>(c, hop);
+  return c->rs == 8 ? launch_t<3, double>(c, hop) : launch_t<3, float>(c, hop);
+}
+
+}  // namespace glasma

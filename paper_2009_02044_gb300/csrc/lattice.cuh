@@ -1,0 +1,157 @@
+// Lattice geometry, structure-of-arrays field access and the plaquette force
+// shared by the step and observable kernels.
+//
+// Layout in device memory (V = nz*ny*nx sites, site s = (iz*ny + iy)*nx + ix,
+// x fastest; x, y periodic, z open):
+//   links  U[(d*NV + k)*V + s]   complex component k of link d at site s,
+//                                stored as float2 / double2
+//                                (SU(2): k = alpha, beta; SU(3): row-major 3x3)
+//   fields E[(d*NA + a)*V + s]   algebra component a of E_d at site s
+//   charges Q[(a*W + w)*nxy + t] component a, window slot w, transverse t
+// The z link of the last slice does not exist: it is stored as the identity
+// and never updated, and E_z there is zero.
+#pragma once
+#include <stdint.h>
+
+#include "su_n.cuh"
+
+namespace glasma {
+
+template <typename R> struct V2T;
+template <> struct V2T<float> { typedef float2 T; };
+template <> struct V2T<double> { typedef double2 T; };
+
+struct Geom {
+  int nx, ny, nz;
+  int64_t nxy, V;
+};
+
+GL_HD int64_t site_index(const Geom& g, int ix, int iy, int iz) {
+  return ((int64_t)iz * g.ny + iy) * g.nx + ix;
+}
+
+// site x + dx e_x + dy e_y + dz e_z (periodic in x, y; caller checks z)
+GL_HD int64_t shifted(const Geom& g, int ix, int iy, int iz, int dx, int dy, int dz) {
+  int x = ix + dx, y = iy + dy;
+  if (x < 0) x += g.nx;
+  if (x >= g.nx) x -= g.nx;
+  if (y < 0) y += g.ny;
+  if (y >= g.ny) y -= g.ny;
+  return site_index(g, x, y, iz + dz);
+}
+
+template <int NC, typename R> struct LinkIO;
+
+template <typename R>
+struct LinkIO<2, R> {
+  template <typename Rc>
+  GL_HD static typename Group<2, Rc>::M load(const typename V2T<R>::T* U, int d, int64_t V, int64_t s) {
+    typename V2T<R>::T a = U[(int64_t)(d * 2 + 0) * V + s];
+    typename V2T<R>::T b = U[(int64_t)(d * 2 + 1) * V + s];
+    return typename Group<2, Rc>::M{{Rc(a.x), Rc(a.y)}, {Rc(b.x), Rc(b.y)}};
+  }
+  template <typename Rc>
+  GL_HD static void store(typename V2T<R>::T* U, int d, int64_t V, int64_t s, const typename Group<2, Rc>::M& m) {
+    typename V2T<R>::T a, b;
+    a.x = R(m.a.re); a.y = R(m.a.im);
+    b.x = R(m.b.re); b.y = R(m.b.im);
+    U[(int64_t)(d * 2 + 0) * V + s] = a;
+    U[(int64_t)(d * 2 + 1) * V + s] = b;
+  }
+};
+
+template <typename R>
+struct LinkIO<3, R> {
+  template <typename Rc>
+  GL_HD static typename Group<3, Rc>::M load(const typename V2T<R>::T* U, int d, int64_t V, int64_t s) {
+    typename Group<3, Rc>::M m;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      typename V2T<R>::T v = U[(int64_t)(d * 9 + k) * V + s];
+      m.m[k] = cplx<Rc>{Rc(v.x), Rc(v.y)};
+    }
+    return m;
+  }
+  template <typename Rc>
+  GL_HD static void store(typename V2T<R>::T* U, int d, int64_t V, int64_t s, const typename Group<3, Rc>::M& m) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      typename V2T<R>::T v;
+      v.x = R(m.m[k].re);
+      v.y = R(m.m[k].im);
+      U[(int64_t)(d * 9 + k) * V + s] = v;
+    }
+  }
+};
+
+// Coordinates and neighbour indices of one site.
+struct SiteNbr {
+  int ix, iy, iz;
+  int64_t s;
+  int64_t p[3];  // x + e_d
+  int64_t m[3];  // x - e_d
+};
+
+GL_HD SiteNbr site_nbr(const Geom& g, int64_t s) {
+  SiteNbr n;
+  n.s = s;
+  n.ix = (int)(s % g.nx);
+  int64_t t = s / g.nx;
+  n.iy = (int)(t % g.ny);
+  n.iz = (int)(t / g.ny);
+  n.p[0] = n.ix + 1 == g.nx ? s - (g.nx - 1) : s + 1;
+  n.m[0] = n.ix == 0 ? s + (g.nx - 1) : s - 1;
+  n.p[1] = n.iy + 1 == g.ny ? s - (int64_t)(g.ny - 1) * g.nx : s + g.nx;
+  n.m[1] = n.iy == 0 ? s + (int64_t)(g.ny - 1) * g.nx : s - g.nx;
+  n.p[2] = s + g.nxy;  // valid for iz <= nz-2
+  n.m[2] = s - g.nxy;  // valid for iz >= 1
+  return n;
+}
+
+// Index of x + e_i - e_j for i != j.
+GL_HD int64_t diag_pm(const Geom& g, const SiteNbr& n, int i, int j) {
+  int d[3] = {0, 0, 0};
+  d[i] += 1;
+  d[j] -= 1;
+  return shifted(g, n.ix, n.iy, n.iz, d[0], d[1], d[2]);
+}
+
+// F^a = -sum_{j != i} w_j [Im tr t^a U_{i,j}(x) + Im tr t^a U_{i,-j}(x)]
+// (Sec. 3, Eq. lattice_1 with Eq. plaquette; w_j = 2 / a_j^2), with the
+// plaquettes that leave the open z range omitted.  Uo[] are the three links
+// at x (already loaded); the caller guarantees that link i exists at x.
+template <int NC, typename Rs, typename Rc>
+GL_HD void link_force(const typename V2T<Rs>::T* U, const Geom& g, const SiteNbr& n,
+                      const typename Group<NC, Rc>::M* Uo, int i, const Rc* w, Rc* F) {
+  typedef Group<NC, Rc> G;
+  typedef typename G::M M;
+  constexpr int NA = G::NA;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) F[a] = Rc(0);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (j == i) continue;
+    Rc pr[NA];
+    bool fwd = (j != 2) || (n.iz <= g.nz - 2);
+    bool bwd = (j != 2) || (n.iz >= 1);
+    if (fwd) {
+      M ujxi = LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.p[i]);
+      M uixj = LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.p[j]);
+      M P = G::mul_d(G::mul_d(G::mul(Uo[i], ujxi), uixj), Uo[j]);
+      G::proj(P, pr);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) F[a] -= w[j] * pr[a];
+    }
+    if (bwd) {
+      M ujd = LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, diag_pm(g, n, i, j));
+      M uixm = LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.m[j]);
+      M ujxm = LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.m[j]);
+      M P = G::mul(G::mul_d(G::mul_d(Uo[i], ujd), uixm), ujxm);
+      G::proj(P, pr);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) F[a] -= w[j] * pr[a];
+    }
+  }
+}
+
+}  // namespace glasma

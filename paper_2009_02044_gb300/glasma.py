@@ -1,0 +1,313 @@
+"""Python binding of the C ABI in include/glasma.h (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of libglasma.so.  PyTorch provides the device memory (through the
+caching allocator, passed to the library as its allocator callbacks) and
+the CUDA stream.  If the shared library is missing the import fails loudly;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libglasma.so")
+
+GLASMA_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NONFINITE",
+    -5: "PARTICLE_EXIT", -6: "NOT_CONVERGED", -7: "TIMEOUT", -8: "CHECKSUM",
+    -9: "INTERNAL",
+}
+FP64, FP32 = 0, 1
+LEAPFROG, IMPLICIT = 0, 1
+
+
+class GlasmaError(RuntimeError):
+    def __init__(self, status, fn, msg):
+        self.status = status
+        self.code = ERRORS.get(status, str(status))
+        super().__init__("%s failed: %s (%s)" % (fn, self.code, msg))
+
+
+class glasma_params(C.Structure):
+    _fields_ = [("nc", C.c_int), ("nz", C.c_int), ("nx", C.c_int),
+                ("ny", C.c_int), ("a_t", C.c_double), ("a_z", C.c_double),
+                ("dt", C.c_double), ("sigma_l", C.c_double),
+                ("g2mu", C.c_double), ("m_ir", C.c_double),
+                ("uv_cutoff", C.c_double), ("z_offset", C.c_double),
+                ("seed", C.c_ulonglong), ("precision", C.c_int),
+                ("scheme", C.c_int), ("implicit_max_iter", C.c_int),
+                ("implicit_tol", C.c_double)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class glasma_allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", C.c_void_p)]
+
+
+class glasma_info(C.Structure):
+    _fields_ = [("sites", C.c_longlong), ("step_n", C.c_longlong),
+                ("nc", C.c_int), ("precision", C.c_int), ("scheme", C.c_int),
+                ("window_a", C.c_int * 2), ("window_b", C.c_int * 2),
+                ("state_device_bytes", C.c_size_t),
+                ("kernel_launches", C.c_int), ("implicit_iters", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libglasma.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "libglasma.so not found at %s: build it first "
+            "(python -m paper_2009_02044_gb300.build)" % path)
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "glasma_init_mv": (C.c_int, [C.POINTER(glasma_params), dp, P,
+                                     C.POINTER(glasma_allocator),
+                                     C.POINTER(C.c_void_p)]),
+        "glasma_step": (C.c_int, [P, C.c_int]),
+        "glasma_gauss_residual": (C.c_int, [P, dp, dp, dp]),
+        "glasma_tmunu": (C.c_int, [P, dp, dp]),
+        "glasma_free": (None, [P]),
+        "glasma_strerror": (C.c_char_p, [C.c_int]),
+        "glasma_last_error_message": (C.c_char_p, []),
+        "glasma_get_fields": (C.c_int, [P, dp, dp, dp, dp,
+                                        C.POINTER(C.c_longlong)]),
+        "glasma_set_fields": (C.c_int, [P, dp, dp, dp, dp, dp, C.c_longlong]),
+        "glasma_state_bytes": (C.c_int, [P, C.POINTER(C.c_size_t)]),
+        "glasma_get_state": (C.c_int, [P, P, C.c_size_t]),
+        "glasma_set_state": (C.c_int, [P, P, C.c_size_t]),
+        "glasma_get_info": (C.c_int, [P, C.POINTER(glasma_info)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, fn):
+    if status != GLASMA_OK:
+        msg = load_library().glasma_last_error_message().decode()
+        raise GlasmaError(status, fn, msg)
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_params(cfg):
+    """glasma_params from a config dict (keys as in glasma_inputs)."""
+    p = glasma_params()
+    p.nc = int(cfg["nc"])
+    p.nz, p.nx, p.ny = int(cfg["nz"]), int(cfg["nx"]), int(cfg["ny"])
+    p.a_t = float(cfg.get("a_t", 1.0))
+    p.a_z = float(cfg.get("a_z", 1.0))
+    p.dt = float(cfg["dt"])
+    p.sigma_l = float(cfg["sigma_l"])
+    p.g2mu = float(cfg["g2mu"])
+    p.m_ir = float(cfg["m_ir"])
+    p.uv_cutoff = float(cfg.get("uv_cutoff", 0.0))
+    p.z_offset = float(cfg.get("z_offset", 0.0))
+    p.seed = int(cfg.get("seed", 0))
+    prec = cfg.get("precision", "fp64")
+    p.precision = FP32 if prec in ("fp32", FP32) else FP64
+    sch = cfg.get("scheme", "leapfrog")
+    p.scheme = IMPLICIT if sch in ("implicit", IMPLICIT) else LEAPFROG
+    p.implicit_max_iter = int(cfg.get("implicit_max_iter", 50))
+    p.implicit_tol = float(cfg.get("implicit_tol", 1e-14))
+    return p
+
+
+# --- PyTorch as the device-memory provider --------------------------------
+
+_live_blocks = {}
+
+
+def _torch_allocator():
+    import torch
+
+    @_ALLOC_FN
+    def _alloc(nbytes, stream, user):
+        try:
+            ptr = torch.cuda.caching_allocator_alloc(
+                int(nbytes), torch.cuda.current_device(),
+                int(stream or 0) or torch.cuda.current_stream())
+        except Exception:
+            return None
+        _live_blocks[ptr] = nbytes
+        return ptr
+
+    @_FREE_FN
+    def _free(ptr, nbytes, stream, user):
+        if ptr in _live_blocks:
+            del _live_blocks[ptr]
+            torch.cuda.caching_allocator_delete(ptr)
+
+    a = glasma_allocator()
+    a.alloc = _alloc
+    a.free = _free
+    a.user = None
+    return a, (_alloc, _free)
+
+
+# --- the C calls, same names ------------------------------------------------
+
+def glasma_init_mv(cfg, rho=None, stream=None, torch_memory=True):
+    """Create a context with the MV initial state; returns an opaque handle.
+
+    rho: None (draw from cfg['seed'] on the device) or float64 array
+    [2][nc^2-1][ny][nx].  stream: a torch.cuda.Stream, a raw cudaStream_t
+    integer or None (torch's current stream)."""
+    lib = load_library()
+    p = make_params(cfg)
+    if rho is not None:
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        na = p.nc * p.nc - 1
+        if rho.shape != (2, na, p.ny, p.nx):
+            raise ValueError("rho must have shape (2, %d, %d, %d)"
+                             % (na, p.ny, p.nx))
+    keep = None
+    alloc_ptr = None
+    if torch_memory:
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        a, keep = _torch_allocator()
+        alloc_ptr = C.byref(a)
+        keep = (a, keep)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    out = C.c_void_p()
+    st = lib.glasma_init_mv(C.byref(p), _dptr(rho), C.c_void_p(s or 0),
+                            alloc_ptr, C.byref(out))
+    _check(st, "glasma_init_mv")
+    return Handle(out, p, keep)
+
+
+class Handle:
+    """Owns one glasma_ctx*; frees it when closed or collected."""
+
+    def __init__(self, ptr, params, keep):
+        self.ptr = ptr
+        self.params = params
+        self._keep = keep
+
+    @property
+    def na(self):
+        return self.params.nc * self.params.nc - 1
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            load_library().glasma_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def glasma_step(h, n_steps):
+    _check(load_library().glasma_step(h.ptr, int(n_steps)), "glasma_step")
+
+
+def glasma_gauss_residual(h):
+    m, r, q = C.c_double(), C.c_double(), C.c_double()
+    _check(load_library().glasma_gauss_residual(h.ptr, C.byref(m), C.byref(r),
+                                                C.byref(q)),
+           "glasma_gauss_residual")
+    return m.value, r.value, q.value
+
+
+def glasma_tmunu(h):
+    tab = np.empty((h.params.nz, 4))
+    H = C.c_double()
+    _check(load_library().glasma_tmunu(h.ptr, _dptr(tab), C.byref(H)),
+           "glasma_tmunu")
+    return tab, H.value
+
+
+def glasma_get_fields(h):
+    p = h.params
+    V = p.nz * p.ny * p.nx
+    na, nc = h.na, p.nc
+    U = np.empty((3, p.nz, p.ny, p.nx, nc, nc, 2))
+    E = np.empty((3, p.nz, p.ny, p.nx, na))
+    QA = np.empty((p.nz, p.ny, p.nx, na))
+    QB = np.empty((p.nz, p.ny, p.nx, na))
+    n = C.c_longlong()
+    _check(load_library().glasma_get_fields(h.ptr, _dptr(U), _dptr(E),
+                                            _dptr(QA), _dptr(QB), C.byref(n)),
+           "glasma_get_fields")
+    assert U.size == 3 * V * nc * nc * 2
+    return U[..., 0] + 1j * U[..., 1], E, QA, QB, n.value
+
+
+def glasma_set_fields(h, U, E, QA=None, QB=None, U_prev=None, step_n=0):
+    def links(u):
+        if u is None:
+            return None
+        u = np.asarray(u)
+        return np.ascontiguousarray(np.stack([u.real, u.imag], -1),
+                                    dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    QA = None if QA is None else np.ascontiguousarray(QA, dtype=np.float64)
+    QB = None if QB is None else np.ascontiguousarray(QB, dtype=np.float64)
+    Ul, Upl = links(U), links(U_prev)
+    _check(load_library().glasma_set_fields(h.ptr, _dptr(Ul), _dptr(E),
+                                            _dptr(QA), _dptr(QB), _dptr(Upl),
+                                            int(step_n)),
+           "glasma_set_fields")
+
+
+def glasma_state_bytes(h):
+    n = C.c_size_t()
+    _check(load_library().glasma_state_bytes(h.ptr, C.byref(n)),
+           "glasma_state_bytes")
+    return n.value
+
+
+def glasma_get_state(h):
+    buf = np.empty(glasma_state_bytes(h), dtype=np.uint8)
+    _check(load_library().glasma_get_state(h.ptr, buf.ctypes.data_as(C.c_void_p),
+                                           buf.nbytes), "glasma_get_state")
+    return buf
+
+
+def glasma_set_state(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load_library().glasma_set_state(h.ptr, buf.ctypes.data_as(C.c_void_p),
+                                           buf.nbytes), "glasma_set_state")
+
+
+def glasma_get_info(h):
+    info = glasma_info()
+    _check(load_library().glasma_get_info(h.ptr, C.byref(info)),
+           "glasma_get_info")
+    return info
+
+
+def glasma_free(h):
+    h.close()
+
+
+def glasma_strerror(status):
+    return load_library().glasma_strerror(int(status)).decode()

@@ -1,0 +1,64 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every
+symbol that include/glasma.h declares, and rejects bad parameters before
+touching the GPU."""
+import os
+import re
+
+import pytest
+
+import glasma_inputs as gi
+from paper_2009_02044_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_2009_02044_gb300 import glasma as G
+    return G.load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "glasma.h")).read()
+    return sorted(set(re.findall(r"GLASMA_API\s+[\w\s\*]+?\b(glasma_\w+)\s*\(",
+                                 src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for need in ("glasma_init_mv", "glasma_step", "glasma_gauss_residual",
+                 "glasma_tmunu", "glasma_free"):
+        assert need in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB],
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (glasma_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    for n in _declared():
+        getattr(lib, n)
+
+
+def test_strerror(lib):
+    from paper_2009_02044_gb300 import glasma as G
+    assert G.glasma_strerror(0) == "ok"
+    assert "invalid" in G.glasma_strerror(-1)
+    assert G.glasma_strerror(-5).startswith("charge")
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nc=4), dict(nz=1), dict(dt=2.0), dict(dt=0.3, a_z=0.9),
+    dict(m_ir=0.0), dict(sigma_l=-1.0), dict(nz=20),
+    dict(g2mu=-1.0), dict(z_offset=1.0),
+])
+def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
+    from paper_2009_02044_gb300 import glasma as G
+    cfg = gi.small_config(2)
+    cfg.update(bad)
+    with pytest.raises(G.GlasmaError) as e:
+        G.glasma_init_mv(cfg, torch_memory=False)
+    assert e.value.code == "INVALID_ARG"

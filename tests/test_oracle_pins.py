@@ -400,11 +400,11 @@ def test_nonabelian_energy_error_is_second_order():
     """Free non-abelian fields: the time-averaged energy fluctuates by
     O(dt^2); halving dt shrinks the excursion about four-fold."""
     rng = np.random.default_rng(9)
-    base = O.Params(nc=2, nz=10, nx=6, ny=6, a_z=1.0, dt=0.2)
+    base = O.Params(nc=2, nz=10, nx=6, ny=6, a_z=1.0, dt=0.25)
     U = gi.near_identity_su(2, (3, base.nz, base.ny, base.nx), rng, 0.25)
     U[2][base.nz - 1] = np.eye(2)
     dev = []
-    for dt in (0.2, 0.1):
+    for dt in (0.25, 0.125):
         p = O.Params(nc=2, nz=10, nx=6, ny=6, a_z=1.0, dt=dt)
         z = np.zeros((p.nz, p.ny, p.nx, 3))
         st = O.State(p, U.copy(), np.zeros((3, p.nz, p.ny, p.nx, 3)),
@@ -477,6 +477,23 @@ def test_init_structure(nc):
     # B's field is behind it (low z), A's behind it (high z)
     assert np.max(np.abs(st.U[0][0] - np.eye(nc))) > 1e-3
     assert np.max(np.abs(st.U[0][p.nz - 1] - np.eye(nc))) > 1e-3
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_plaquette_energy_forms_agree(nc):
+    """||U_i U_j(x+i) - U_j U_i(x+j)||_F^2 = 2 (N - Re tr U_ij) for unitary
+    links: both forms agree to rounding on generic and on weak fields."""
+    rng = np.random.default_rng(31)
+    p = O.Params(nc=nc, nz=6, nx=4, ny=5, a_z=0.5)
+    for amp in (0.5, 1e-3):
+        U = gi.near_identity_su(nc, (3, p.nz, p.ny, p.nx), rng, amp)
+        U[2][p.nz - 1] = np.eye(nc)
+        bf = O.plaquette_terms(U, p)
+        bt = O.plaquette_terms_trace(U, p)
+        for k in bf:
+            assert np.max(np.abs(bf[k] - bt[k])) < 5e-14 / (
+                p.spacing[k[0]] * p.spacing[k[1]]) ** 2
+        assert np.max(bf[(0, 1)]) > 0
 
 
 def test_vacuum_stays_vacuum():
