@@ -158,6 +158,40 @@ GLASMA_API int glasma_gauss_residual(glasma_ctx* c, double* max_abs, double* rms
  */
 GLASMA_API int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total);
 
+/*
+ * Gauss-law residual of fields the caller owns, computed without allocating
+ * any device memory.  The paper has no counterpart of this call: it exists
+ * for callers that cannot call cudaMalloc -- for example a health check that
+ * must still run after the device has run out of memory, or code inside a
+ * framework whose allocator owns all device memory and forbids raw
+ * allocations (a raw cudaMalloc can also synchronise the device).
+ * It computes the same quantity as glasma_gauss_residual.
+ * Inputs are device pointers in the library's layout (x fastest, site
+ * s = (iz*ny + iy)*nx + ix, V = nz*ny*nx; R = double for GLASMA_FP64,
+ * float for GLASMA_FP32):
+ *   U  links, complex component k of link d at U[(d*NV + k)*V + s] as
+ *      (re, im) pairs of R; SU(2): NV = 2, (alpha, beta) of
+ *      [[alpha, beta], [-beta*, alpha*]]; SU(3): NV = 9, row-major 3x3;
+ *   E  fields, E[(d*(nc^2-1) + a)*V + s];
+ *   QA, QB charge windows of zA0.. zA0+WA-1 and zB0.. zB0+WB-1 (z slices),
+ *      Q[(a*W + w)*nx*ny + t]; a pointer may be NULL when its W is 0.
+ * Outputs are host doubles (any may be NULL), as in glasma_gauss_residual.
+ * Scratch: a fixed device array inside the library, one row of partials
+ * per z slice, so nz may be at most 8192; larger nz is rejected with
+ * GLASMA_ERR_INVALID_ARG before any GPU work.  Every GPU that loads the
+ * library keeps that array (256 KB) until the process exits.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Work runs on
+ * `stream` (cudaStream_t, NULL = legacy default), which the call
+ * synchronises.  Errors: INVALID_ARG, NONFINITE, CUDA.
+ */
+GLASMA_API int glasma_gauss_residual_static(int nc, int precision, int nz, int ny, int nx, double a_t,
+                                            double a_z, const void* U, const void* E, const void* QA,
+                                            int zA0, int WA, const void* QB, int zB0, int WB,
+                                            void* stream, double* max_abs, double* rms, double* rho_max);
+
 /* Release every device buffer of the context (stream-ordered) and the
  * context itself.  NULL is ignored. */
 GLASMA_API void glasma_free(glasma_ctx* c);

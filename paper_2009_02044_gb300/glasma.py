@@ -92,6 +92,10 @@ def load_library(path=LIB_PATH):
         "glasma_get_state": (C.c_int, [P, P, C.c_size_t]),
         "glasma_set_state": (C.c_int, [P, P, C.c_size_t]),
         "glasma_get_info": (C.c_int, [P, C.POINTER(glasma_info)]),
+        "glasma_gauss_residual_static": (
+            C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                      C.c_double, C.c_double, P, P, P, C.c_int, C.c_int, P,
+                      C.c_int, C.c_int, P, dp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -311,3 +315,20 @@ def glasma_free(h):
 
 def glasma_strerror(status):
     return load_library().glasma_strerror(int(status)).decode()
+
+
+def glasma_gauss_residual_static(nc, precision, nz, ny, nx, a_t, a_z, U, E,
+                                 QA=None, zA0=0, WA=0, QB=None, zB0=0, WB=0,
+                                 stream=None):
+    """Gauss residual of caller-owned device fields with no device
+    allocation (see include/glasma.h).  U, E, QA, QB are raw device
+    addresses (ints) in the library's layout; returns (max, rms, rho_max)."""
+    m, r, q = C.c_double(), C.c_double(), C.c_double()
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    prec = FP32 if precision in ("fp32", FP32) else FP64
+    _check(load_library().glasma_gauss_residual_static(
+        int(nc), prec, int(nz), int(ny), int(nx), float(a_t), float(a_z),
+        C.c_void_p(U), C.c_void_p(E), C.c_void_p(QA), int(zA0), int(WA),
+        C.c_void_p(QB), int(zB0), int(WB), C.c_void_p(s or 0),
+        C.byref(m), C.byref(r), C.byref(q)), "glasma_gauss_residual_static")
+    return m.value, r.value, q.value
