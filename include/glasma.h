@@ -76,7 +76,9 @@ typedef struct {
                                fields; every reduction in FP64) */
   int scheme;               /* GLASMA_LEAPFROG or GLASMA_IMPLICIT */
   int implicit_max_iter;    /* fixed-point iterations of the implicit scheme */
-  double implicit_tol;      /* its convergence threshold on max |dE| */
+  double implicit_tol;      /* its convergence threshold on max |dE|; the
+                               iteration also ends when max |dE| stops
+                               decreasing (the precision's rounding floor) */
 } glasma_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both

@@ -188,7 +188,9 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
   c->E = ctx_alloc(c, eb);
   if (p->scheme == GLASMA_IMPLICIT) {
     c->Uprev = ctx_alloc(c, ub);
+    c->Uit = ctx_alloc(c, ub);
     c->Ework = ctx_alloc(c, eb);
+    c->conv = (double*)ctx_alloc(c, sizeof(double) * (p->implicit_max_iter + 1));
   }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -197,7 +199,7 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
   c->tab = (double*)ctx_alloc(c, sizeof(double) * 4 * p->nz);
   c->dflag = (int*)ctx_alloc(c, sizeof(int) * 8);
   if (!c->U[0] || !c->U[1] || !c->E || !c->red || !c->tab || !c->dflag ||
-      (p->scheme == GLASMA_IMPLICIT && (!c->Uprev || !c->Ework))) {
+      (p->scheme == GLASMA_IMPLICIT && (!c->Uprev || !c->Uit || !c->Ework || !c->conv))) {
     glasma_free(c);
     return set_error(GLASMA_ERR_OOM, "state allocation failed");
   }
@@ -234,13 +236,18 @@ int glasma_step(glasma_ctx* c, int n_steps) {
       st = launch_step_leapfrog(c, hop);
       launches += 1;
     }
-    if (st) return st;
-    c->cur = 1 - c->cur;
+    // a step that did not converge has still been taken (last iterate kept)
+    if (st && st != GLASMA_ERR_NOT_CONVERGED) return st;
+    if (c->p.scheme != GLASMA_IMPLICIT) c->cur = 1 - c->cur;  // the implicit launcher rotates its buffers
     if (hop) {
       c->zB0 += 1;
       c->zA0 -= 1;
     }
     c->n += 1;
+    if (st) {
+      c->last_launches = launches;
+      return st;
+    }
   }
   c->last_launches = launches;
   return GLASMA_OK;
@@ -483,15 +490,20 @@ int glasma_set_fields(glasma_ctx* c, const double* U, const double* E, const dou
     st = reals_to_dev(c, c->E, raw.data(), raw.size());
     if (st) return st;
   }
+  if (c->Uit) {
+    st = upload_links(c, c->Uit, U);
+    if (st) return st;
+  }
   if (c->Uprev) {
     if (U_prev) {
       st = upload_links(c, c->Uprev, U_prev);
+      if (st) return st;
+      c->uprev_valid = true;
     } else {
-      // exp(-i dt E) U on the host would duplicate device arithmetic; the
-      // implicit step rebuilds it on first use instead
-      st = cuda_check(cudaMemsetAsync(c->Uprev, 0, 2 * c->rs * 3 * (size_t)c->nv * V, c->stream), "Uprev clear");
+      // the first implicit step rebuilds U(t_{n-1}) = exp(-i dt E) U(t_n)
+      // on the device
+      c->uprev_valid = false;
     }
-    if (st) return st;
   }
   const double* qh[2] = {QA, QB};
   int* z0[2] = {&c->zA0, &c->zB0};
@@ -657,9 +669,14 @@ int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes) {
     }
     off += sizes[k] + sizeof(uint32_t);
   }
-  // the other link buffer needs the identity z links of the last slice
+  // the other link buffers need the identity z links of the last slice
   st = cuda_check(cudaMemcpyAsync(c->U[1], c->U[0], sizes[0], cudaMemcpyDeviceToDevice, c->stream), "state copy");
   if (st) return st;
+  if (c->Uit) {
+    st = cuda_check(cudaMemcpyAsync(c->Uit, c->U[0], sizes[0], cudaMemcpyDeviceToDevice, c->stream), "state copy");
+    if (st) return st;
+    c->uprev_valid = true;
+  }
   c->zA0 = h.zA0;
   c->zB0 = h.zB0;
   c->n = h.n;

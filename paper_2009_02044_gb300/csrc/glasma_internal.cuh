@@ -22,8 +22,11 @@ struct glasma_ctx {
   void* U[2] = {nullptr, nullptr};
   int cur = 0;                // U[cur] holds U(t_n)
   void* Uprev = nullptr;      // U(t_{n-1}), implicit scheme only
+  void* Uit = nullptr;        // implicit scheme: second iterate buffer of U(t_{n+1})
+  bool uprev_valid = false;   // Uprev holds U(t_{n-1})
   void* E = nullptr;          // E(t_{n-1/2})
-  void* Ework = nullptr;      // implicit scheme: E(t_{n-1/2}) kept during iteration
+  void* Ework = nullptr;      // implicit scheme: E(t_{n-1/2}) + current, fixed during iteration
+  double* conv = nullptr;     // implicit scheme: max |dE| of each iteration
   void* QA = nullptr;         // charge windows (co-moving slots)
   void* QB = nullptr;
   int zA0 = 0, WA = 0, zB0 = 0, WB = 0;  // first slice and slices of each window

@@ -1,13 +1,296 @@
-// Semi-implicit step (placeholder until the scheme's kernels land).
+// Semi-implicit step against the numerical Cherenkov instability (Sec. 3,
+// the paragraph after Eq. gauss, Fig. wilson (b); Sec. 5).
+//
+// Each staple pair U_{i,+-j} of Eq. lattice_1 is replaced by its average over
+// the time slots m = n+1, n, n-1 with weights (1/4, 1/2, 1/4).  In the
+// transverse plane (x, y) every link of the loop is taken at slot m; in a
+// plane containing z only the z links are taken at slot m and the transverse
+// links stay at t_n.  The system is solved by fixed-point iteration on
+// E(t_{n+1/2}) starting from U(t_{n+1}) = exp(i dt E(t_{n-1/2})) U(t_n).
+// The CPIC hop and its current are those of the leapfrog step (they use
+// U(t_n) only) and are applied once, before the iteration.
+//
+// Buffers: Uprev = U(t_{n-1}), U[cur] = U(t_n), the other U buffer and Uit
+// hold the iterates of U(t_{n+1}); E is iterated in place, Ework keeps
+// E(t_{n-1/2}) + dt J.  conv[k] is the largest |E^(k+1) - E^(k)| of
+// iteration k (atomicMax on the bit pattern of a non-negative double).
+// The iteration ends when that change is below implicit_tol or stops
+// decreasing (the rounding floor of the state's precision, reached first in
+// FP32); stopping above the floor would leave a same-signed truncation error
+// every step, which breaks the time symmetry of the scheme and makes the
+// energy drift.  Iteration k returns at once once either holds.
+#include <vector>
+
 #include "glasma_internal.cuh"
 
 namespace glasma {
 
+template <typename R>
+struct ImplArgs {
+  typedef typename V2T<R>::T V2;
+  const V2* Up;   // U(t_{n-1})
+  const V2* Un;   // U(t_n)
+  const V2* X;    // current iterate of U(t_{n+1})
+  V2* Xn;         // next iterate
+  V2* Uout;       // prepare / previous-link kernels: output links
+  R* E;
+  R* Ework;
+  R* QA;
+  R* QB;
+  double* conv;
+  int k;
+  double tol;
+  Geom g;
+  R dt;
+  R w[3];
+  R az2;
+  int hop;
+  int zA0, WA, zB0, WB;
+};
+
+// Link buffer of slot m for a link of direction d in plane (i, j).
+template <typename R>
+__device__ __forceinline__ const typename V2T<R>::T* slot_buf(const ImplArgs<R>& a, int m, bool zplane, int d) {
+  if (zplane && d != 2) return a.Un;
+  return m == 0 ? a.X : (m == 1 ? a.Un : a.Up);
+}
+
+// Time-averaged force on link i at x.
+template <int NC, typename R>
+__device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R* F) {
+  typedef Group<NC, R> G;
+  typedef typename G::M M;
+  constexpr int NA = G::NA;
+  const R wt[3] = {R(0.25), R(0.5), R(0.25)};
+#pragma unroll
+  for (int c = 0; c < NA; ++c) F[c] = R(0);
+#pragma unroll 1
+  for (int j = 0; j < 3; ++j) {
+    if (j == i) continue;
+    const bool zplane = (i == 2) || (j == 2);
+    const bool fwd = (j != 2) || (n.iz <= a.g.nz - 2);
+    const bool bwd = (j != 2) || (n.iz >= 1);
+#pragma unroll 1
+    for (int m = 0; m < 3; ++m) {
+      const typename V2T<R>::T* Bi = slot_buf(a, m, zplane, i);
+      const typename V2T<R>::T* Bj = slot_buf(a, m, zplane, j);
+      M S = G::zero();
+      if (fwd) {
+        M T = G::mul_d(LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.p[i]),
+                       LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.p[j]));
+        T = G::mul_d(T, LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.s));
+        G::scale_add(S, R(1), T);
+      }
+      if (bwd) {
+        M T = G::mul(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.m[j]),
+                     LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, diag_pm(a.g, n, i, j)));
+        T = G::d_mul(T, LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.m[j]));
+        G::scale_add(S, R(1), T);
+      }
+      R pr[NA];
+      G::proj_mul(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.s), S, pr);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) F[c] -= a.w[j] * wt[m] * pr[c];
+    }
+  }
+}
+
+// U(t_{n-1}) = exp(-i dt E(t_{n-1/2})) U(t_n), when it is not known.
+template <int NC, typename R>
+__global__ void __launch_bounds__(128) k_implicit_prev(ImplArgs<R> a) {
+  typedef Group<NC, R> G;
+  constexpr int NA = G::NA;
+  const int i = blockIdx.y;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.g.V) return;
+  if (i == 2 && (int)(s / a.g.nxy) == a.g.nz - 1) return;
+  R e[NA];
+#pragma unroll
+  for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
+  typename G::M u = G::mul(G::expi(e, -a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
+  if (sizeof(R) == 4) u = G::reunit(u);
+  LinkIO<NC, R>::template store<R>(a.Uout, i, a.g.V, s, u);
+}
+
+// Hop (charges committed, current into Ework) and the first iterate.
+template <int NC, typename R>
+__global__ void __launch_bounds__(128) k_implicit_prep(ImplArgs<R> a) {
+  typedef Group<NC, R> G;
+  typedef typename G::M M;
+  constexpr int NA = G::NA;
+  const int i = blockIdx.y;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.g.V) return;
+  const int iz = (int)(s / a.g.nxy);
+  if (i == 2 && iz == a.g.nz - 1) return;
+  const M Ui = LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s);
+  R e[NA], ew[NA];
+#pragma unroll
+  for (int c = 0; c < NA; ++c) ew[c] = e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
+  if (i == 2 && a.hop) {
+    const int64_t t = s % a.g.nxy;
+    const int kb = iz - a.zB0;
+    R dj[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) dj[c] = R(0);
+    if (kb >= 0 && kb < a.WB) {
+      R q[NA];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) q[c] = a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) dj[c] -= a.az2 * q[c];
+      G::adj_dag(Ui, q);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t] = q[c];
+    }
+    const int ka = iz + 1 - a.zA0;
+    if (ka >= 0 && ka < a.WA) {
+      R q[NA];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
+      G::adj(Ui, q);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) {
+        dj[c] += a.az2 * q[c];
+        a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t] = q[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NA; ++c) ew[c] += dj[c];
+  }
+#pragma unroll
+  for (int c = 0; c < NA; ++c) a.Ework[(int64_t)(i * NA + c) * a.g.V + s] = ew[c];
+  M u = G::mul(G::expi(e, a.dt), Ui);
+  if (sizeof(R) == 4) u = G::reunit(u);
+  LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
+}
+
+// One fixed-point sweep: E = Ework + dt F(U_{n-1}, U_n, X), Xn = exp(i dt E) U_n.
+template <int NC, typename R>
+__global__ void __launch_bounds__(128, 2) k_implicit_iter(ImplArgs<R> a) {
+  typedef Group<NC, R> G;
+  typedef typename G::M M;
+  constexpr int NA = G::NA;
+  // converged earlier: below the tolerance, or no longer decreasing (the
+  // rounding floor of the state's precision)
+  if (a.k > 0 && a.conv[a.k - 1] < a.tol) return;
+  if (a.k > 1 && a.conv[a.k - 1] >= a.conv[a.k - 2]) return;
+  __shared__ double smax[128];
+  const int i = blockIdx.y;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double dmax = 0.0;
+  const bool live = s < a.g.V && !(i == 2 && (int)(s / a.g.nxy) == a.g.nz - 1);
+  if (live) {
+    SiteNbr n = site_nbr(a.g, s);
+    R F[NA];
+    force_implicit<NC, R>(a, n, i, F);
+    R e[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) {
+      const int64_t idx = (int64_t)(i * NA + c) * a.g.V + s;
+      e[c] = a.Ework[idx] + a.dt * F[c];
+      const double d = fabs((double)e[c] - (double)a.E[idx]);
+      dmax = isfinite(d) ? fmax(dmax, d) : INFINITY;
+      a.E[idx] = e[c];
+    }
+    M u = G::mul(G::expi(e, a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
+    if (sizeof(R) == 4) u = G::reunit(u);
+    LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
+  }
+  smax[threadIdx.x] = dmax;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    atomicMax((unsigned long long*)&a.conv[a.k], (unsigned long long)__double_as_longlong(smax[0]));
+}
+
+template <int NC, typename R>
+static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
+  typedef typename V2T<R>::T V2;
+  ImplArgs<R> a;
+  a.E = (R*)c->E;
+  a.Ework = (R*)c->Ework;
+  a.QA = (R*)c->QA;
+  a.QB = (R*)c->QB;
+  a.conv = c->conv;
+  a.tol = c->p.implicit_tol;
+  a.g = c->g;
+  a.dt = (R)c->p.dt;
+  a.w[0] = (R)(2.0 / (c->p.a_t * c->p.a_t));
+  a.w[1] = a.w[0];
+  a.w[2] = (R)(2.0 / (c->p.a_z * c->p.a_z));
+  a.az2 = (R)(c->p.a_z * c->p.a_z);
+  a.hop = hop ? 1 : 0;
+  a.zA0 = c->zA0;
+  a.WA = c->WA;
+  a.zB0 = c->zB0;
+  a.WB = c->WB;
+  void* prev = c->Uprev;
+  void* now = c->U[c->cur];
+  void* xa = c->U[1 - c->cur];
+  void* xb = c->Uit;
+  a.Up = (const V2*)prev;
+  a.Un = (const V2*)now;
+  const int bs = 128;
+  const dim3 grid((unsigned)((c->g.V + bs - 1) / bs), 3);
+  int st;
+  if (!c->uprev_valid) {
+    a.Uout = (V2*)prev;
+    k_implicit_prev<NC, R><<<grid, bs, 0, c->stream>>>(a);
+    st = cuda_check(cudaGetLastError(), "k_implicit_prev launch");
+    if (st) return st;
+    c->uprev_valid = true;
+  }
+  const int maxit = c->p.implicit_max_iter;
+  st = cuda_check(cudaMemsetAsync(c->conv, 0, sizeof(double) * (maxit + 1), c->stream), "conv clear");
+  if (st) return st;
+  a.Xn = (V2*)xa;
+  k_implicit_prep<NC, R><<<grid, bs, 0, c->stream>>>(a);
+  st = cuda_check(cudaGetLastError(), "k_implicit_prep launch");
+  if (st) return st;
+  for (int k = 0; k < maxit; ++k) {
+    a.k = k;
+    a.X = (const V2*)(k % 2 == 0 ? xa : xb);
+    a.Xn = (V2*)(k % 2 == 0 ? xb : xa);
+    k_implicit_iter<NC, R><<<grid, bs, 0, c->stream>>>(a);
+    st = cuda_check(cudaGetLastError(), "k_implicit_iter launch");
+    if (st) return st;
+  }
+  std::vector<double> conv(maxit);
+  st = cuda_check(cudaMemcpyAsync(conv.data(), c->conv, sizeof(double) * maxit, cudaMemcpyDeviceToHost, c->stream),
+                  "conv readback");
+  if (st) return st;
+  st = cuda_check(cudaStreamSynchronize(c->stream), "implicit sync");
+  if (st) return st;
+  int done = 0;
+  bool converged = false;
+  for (int k = 0; k < maxit; ++k) {
+    done = k + 1;
+    if (!isfinite(conv[k])) return set_error(GLASMA_ERR_NONFINITE, "implicit iteration met a non-finite value");
+    if (conv[k] < a.tol || (k >= 1 && conv[k] >= conv[k - 1])) {
+      converged = true;
+      break;
+    }
+  }
+  *iters = done;
+  // iteration k writes xb for even k and xa for odd k
+  void* fin = ((done - 1) % 2 == 0) ? xb : xa;
+  void* spare = fin == xa ? xb : xa;
+  c->Uprev = now;
+  c->U[c->cur] = fin;
+  c->U[1 - c->cur] = prev;
+  c->Uit = spare;
+  if (!converged)
+    return set_error(GLASMA_ERR_NOT_CONVERGED, "implicit iteration did not reach implicit_tol within implicit_max_iter");
+  return GLASMA_OK;
+}
+
 int launch_step_implicit(glasma_ctx* c, bool hop, int* iters) {
-  (void)c;
-  (void)hop;
-  *iters = 0;
-  return set_error(GLASMA_ERR_INVALID_ARG, "implicit scheme not available in this build");
+  if (c->p.nc == 2) return c->rs == 8 ? implicit_t<2, double>(c, hop, iters) : implicit_t<2, float>(c, hop, iters);
+  return c->rs == 8 ? implicit_t<3, double>(c, hop, iters) : implicit_t<3, float>(c, hop, iters);
 }
 
 }  // namespace glasma

@@ -320,6 +320,13 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
                                                                                    c->WB, c->g);
   st = cuda_check(cudaGetLastError(), "window fill");
   if (st) return st;
+  if (c->Uit) {  // second iterate buffer of the implicit scheme: identity last-slice z links
+    st = cuda_check(cudaMemcpyAsync(c->Uit, c->U[0], 2 * c->rs * 3 * (size_t)c->nv * V, cudaMemcpyDeviceToDevice,
+                                    c->stream),
+                    "iterate buffer init");
+    if (st) return st;
+    c->uprev_valid = true;
+  }
   st = cuda_check(cudaStreamSynchronize(c->stream), "init sync 2");
   ctx_free(c, rho);
   ctx_free(c, w0);

@@ -1,7 +1,7 @@
 // Fused leapfrog step with the CPIC hop (Sec. 3, Eqs. lattice_1, lattice_2,
 // continuity and the NGP parallel transport).
 //
-// One thread per site.  For each of the site's three links it
+// One thread per link.  For its link it
 //   (1) on a hop step and for the z link: transports the charge of B that
 //       sits at x to x+z (Q' = U_z^dag Q U_z) and the charge of A that sits
 //       at x+z to x (Q' = U_z Q U_z^dag), and deposits dt J_z =
@@ -31,61 +31,67 @@ struct StepArgs {
   int zA0, WA, zB0, WB;
 };
 
+// One thread per link: the block index interleaves the three directions
+// (i = blockIdx.x % 3) so the blocks working on one region of the lattice
+// run together and share its links in L2; a thread holds one link, the
+// staple sum and one neighbour product at a time.
+// FP32 fits 128 registers (4 blocks of 128 threads per SM); FP64 needs
+// twice the registers for the same matrices.
+template <typename R> struct StepOcc { static constexpr int blocks = 4; };
+template <> struct StepOcc<double> { static constexpr int blocks = 2; };
+
 template <int NC, typename R>
-__global__ void __launch_bounds__(128) k_step_leapfrog(StepArgs<R> a) {
+__global__ void __launch_bounds__(128, StepOcc<R>::blocks) k_step_leapfrog(StepArgs<R> a) {
   typedef Group<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(blockIdx.x % 3u);
+  const int64_t s = (int64_t)(blockIdx.x / 3u) * blockDim.x + threadIdx.x;
   if (s >= a.g.V) return;
   SiteNbr n = site_nbr(a.g, s);
-  M Uo[3];
+  if (i == 2 && n.iz == a.g.nz - 1) return;  // no z link on the last slice
+  const M Ui = LinkIO<NC, R>::template load<R>(a.U, i, a.g.V, s);
+  R F[NA];
+  link_force_staple<NC, R, R>(a.U, a.g, n, Ui, i, a.w, F);
+  R e[NA];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) Uo[d] = LinkIO<NC, R>::template load<R>(a.U, d, a.g.V, s);
-  const int ilast = (n.iz == a.g.nz - 1) ? 2 : 3;  // no z link on the last slice
-  for (int i = 0; i < ilast; ++i) {
-    R F[NA];
-    link_force<NC, R, R>(a.U, a.g, n, Uo, i, a.w, F);
-    R e[NA];
+  for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s] + a.dt * F[c];
+  if (i == 2 && a.hop) {
+    const int64_t t = s % a.g.nxy;
+    R dj[NA];
 #pragma unroll
-    for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s] + a.dt * F[c];
-    if (i == 2 && a.hop) {
-      const int64_t t = s % a.g.nxy;
-      R dj[NA];
+    for (int c = 0; c < NA; ++c) dj[c] = R(0);
+    const int kb = n.iz - a.zB0;
+    if (kb >= 0 && kb < a.WB) {
+      R q[NA];
 #pragma unroll
-      for (int c = 0; c < NA; ++c) dj[c] = R(0);
-      const int kb = n.iz - a.zB0;
-      if (kb >= 0 && kb < a.WB) {
-        R q[NA];
+      for (int c = 0; c < NA; ++c) q[c] = a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
 #pragma unroll
-        for (int c = 0; c < NA; ++c) q[c] = a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
+      for (int c = 0; c < NA; ++c) dj[c] -= a.az2 * q[c];
+      G::adj_dag(Ui, q);
 #pragma unroll
-        for (int c = 0; c < NA; ++c) dj[c] -= a.az2 * q[c];
-        G::adj_dag(Uo[2], q);
+      for (int c = 0; c < NA; ++c) a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t] = q[c];
+    }
+    const int ka = n.iz + 1 - a.zA0;
+    if (ka >= 0 && ka < a.WA) {
+      R q[NA];
 #pragma unroll
-        for (int c = 0; c < NA; ++c) a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t] = q[c];
+      for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
+      G::adj(Ui, q);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) {
+        dj[c] += a.az2 * q[c];
+        a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t] = q[c];
       }
-      const int ka = n.iz + 1 - a.zA0;
-      if (ka >= 0 && ka < a.WA) {
-        R q[NA];
-#pragma unroll
-        for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
-        G::adj(Uo[2], q);
-#pragma unroll
-        for (int c = 0; c < NA; ++c) {
-          dj[c] += a.az2 * q[c];
-          a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t] = q[c];
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NA; ++c) e[c] += dj[c];
     }
 #pragma unroll
-    for (int c = 0; c < NA; ++c) a.E[(int64_t)(i * NA + c) * a.g.V + s] = e[c];
-    M un = G::mul(G::expi(e, a.dt), Uo[i]);
-    if (sizeof(R) == 4) un = G::reunit(un);
-    LinkIO<NC, R>::template store<R>(a.Un, i, a.g.V, s, un);
+    for (int c = 0; c < NA; ++c) e[c] += dj[c];
   }
+#pragma unroll
+  for (int c = 0; c < NA; ++c) a.E[(int64_t)(i * NA + c) * a.g.V + s] = e[c];
+  M un = G::mul(G::expi(e, a.dt), Ui);
+  if (sizeof(R) == 4) un = G::reunit(un);
+  LinkIO<NC, R>::template store<R>(a.Un, i, a.g.V, s, un);
 }
 
 template <int NC, typename R>
@@ -109,7 +115,7 @@ static int launch_t(glasma_ctx* c, bool hop) {
   a.WB = c->WB;
   const int bs = 128;
   const int64_t nb = (c->g.V + bs - 1) / bs;
-  k_step_leapfrog<NC, R><<<(unsigned)nb, bs, 0, c->stream>>>(a);
+  k_step_leapfrog<NC, R><<<(unsigned)(3 * nb), bs, 0, c->stream>>>(a);
   return cuda_check(cudaGetLastError(), "k_step_leapfrog launch");
 }
 

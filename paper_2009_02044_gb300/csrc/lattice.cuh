@@ -1,4 +1,4 @@
-// Lattice geometry, structure-of-arrays field access and the plaquette force
+// Lattice geometry, structure-of-arrays field access and the staple force
 // shared by the step and observable kernels.
 //
 // Layout in device memory (V = nz*ny*nx sites, site s = (iz*ny + iy)*nx + ix,
@@ -117,41 +117,42 @@ GL_HD int64_t diag_pm(const Geom& g, const SiteNbr& n, int i, int j) {
 }
 
 // F^a = -sum_{j != i} w_j [Im tr t^a U_{i,j}(x) + Im tr t^a U_{i,-j}(x)]
-// (Sec. 3, Eq. lattice_1 with Eq. plaquette; w_j = 2 / a_j^2), with the
-// plaquettes that leave the open z range omitted.  Uo[] are the three links
-// at x (already loaded); the caller guarantees that link i exists at x.
+// (Sec. 3, Eq. lattice_1 with Eq. plaquette; w_j = 2 / a_j^2), plaquettes
+// that leave the open z range omitted, evaluated from the staple sum:
+// F = -proj(U_i(x) S) with
+// S = sum_j w_j [U_j(x+i) U_i^dag(x+j) U_j^dag(x)
+//                + U_j^dag(x+i-j) U_i^dag(x-j) U_j(x-j)],
+// since Im tr t^a (U_i S) is linear in S.  Only the anti-hermitian part of
+// the last product is formed.
 template <int NC, typename Rs, typename Rc>
-GL_HD void link_force(const typename V2T<Rs>::T* U, const Geom& g, const SiteNbr& n,
-                      const typename Group<NC, Rc>::M* Uo, int i, const Rc* w, Rc* F) {
+GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const SiteNbr& n,
+                             const typename Group<NC, Rc>::M& Ui, int i, const Rc* w, Rc* F) {
   typedef Group<NC, Rc> G;
   typedef typename G::M M;
-  constexpr int NA = G::NA;
-#pragma unroll
-  for (int a = 0; a < NA; ++a) F[a] = Rc(0);
+  M S = G::zero();
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     if (j == i) continue;
-    Rc pr[NA];
-    bool fwd = (j != 2) || (n.iz <= g.nz - 2);
-    bool bwd = (j != 2) || (n.iz >= 1);
+    const bool fwd = (j != 2) || (n.iz <= g.nz - 2);
+    const bool bwd = (j != 2) || (n.iz >= 1);
     if (fwd) {
-      M ujxi = LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.p[i]);
-      M uixj = LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.p[j]);
-      M P = G::mul_d(G::mul_d(G::mul(Uo[i], ujxi), uixj), Uo[j]);
-      G::proj(P, pr);
-#pragma unroll
-      for (int a = 0; a < NA; ++a) F[a] -= w[j] * pr[a];
+      M T = G::mul_d(LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.p[i]),
+                     LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.p[j]));
+      T = G::mul_d(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.s));
+      G::scale_add(S, w[j], T);
     }
     if (bwd) {
-      M ujd = LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, diag_pm(g, n, i, j));
-      M uixm = LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.m[j]);
-      M ujxm = LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.m[j]);
-      M P = G::mul(G::mul_d(G::mul_d(Uo[i], ujd), uixm), ujxm);
-      G::proj(P, pr);
-#pragma unroll
-      for (int a = 0; a < NA; ++a) F[a] -= w[j] * pr[a];
+      M T = G::mul(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.m[j]),
+                   LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, diag_pm(g, n, i, j)));
+      T = G::d_mul(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.m[j]));
+      G::scale_add(S, w[j], T);
     }
   }
+  constexpr int NA = G::NA;
+  Rc pr[NA];
+  G::proj_mul(Ui, S, pr);
+#pragma unroll
+  for (int a = 0; a < NA; ++a) F[a] = -pr[a];
 }
 
 }  // namespace glasma

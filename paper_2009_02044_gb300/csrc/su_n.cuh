@@ -78,6 +78,13 @@ struct Group<2, R> {
     out[2] = x.a.im;  // Im tr(sigma3/2 X)
   }
   GL_HD static R re_tr(const M& x) { return R(2) * x.a.re; }
+  // proj(x y) without forming the unused parts of the product
+  GL_HD static void proj_mul(const M& x, const M& y, R* out) { proj(mul(x, y), out); }
+  GL_HD static void scale_add(M& acc, R w, const M& x) {
+    acc.a = acc.a + w * x.a;
+    acc.b = acc.b + w * x.b;
+  }
+  GL_HD static M zero() { return M{{R(0), R(0)}, {R(0), R(0)}}; }
   // exp(i c sum_a v^a sigma^a/2) = cos(th) + i sin(th) n.sigma, th = c|v|/2
   GL_HD static M expi(const R* v, R c) {
     R n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
@@ -218,6 +225,45 @@ struct Group<3, R> {
     o[7] = (m[0].im + m[4].im - R(2) * m[8].im) * R(0.28867513459481288225);  // 1/(2 sqrt 3)
   }
   GL_HD static R re_tr(const M& x) { return x.m[0].re + x.m[4].re + x.m[8].re; }
+  GL_HD static M zero() {
+    M r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r.m[k] = cplx<R>{R(0), R(0)};
+    return r;
+  }
+  GL_HD static void scale_add(M& acc, R w, const M& x) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc.m[k] = acc.m[k] + w * x.m[k];
+  }
+  // (x y)_ij
+  GL_HD static cplx<R> prod_elem(const M& x, const M& y, int i, int j) {
+    cplx<R> acc = x.m[3 * i] * y.m[j];
+    acc = fma_c(x.m[3 * i + 1], y.m[3 + j], acc);
+    return fma_c(x.m[3 * i + 2], y.m[6 + j], acc);
+  }
+  GL_HD static R prod_diag_im(const M& x, const M& y, int i) {
+    R acc = x.m[3 * i].re * y.m[i].im + x.m[3 * i].im * y.m[i].re;
+    acc = fma(x.m[3 * i + 1].re, y.m[3 + i].im, acc);
+    acc = fma(x.m[3 * i + 1].im, y.m[3 + i].re, acc);
+    acc = fma(x.m[3 * i + 2].re, y.m[6 + i].im, acc);
+    acc = fma(x.m[3 * i + 2].im, y.m[6 + i].re, acc);
+    return acc;
+  }
+  // proj(x y) from the six off-diagonal and three diagonal imaginary parts
+  GL_HD static void proj_mul(const M& x, const M& y, R* o) {
+    const cplx<R> p01 = prod_elem(x, y, 0, 1), p10 = prod_elem(x, y, 1, 0);
+    const cplx<R> p02 = prod_elem(x, y, 0, 2), p20 = prod_elem(x, y, 2, 0);
+    const cplx<R> p12 = prod_elem(x, y, 1, 2), p21 = prod_elem(x, y, 2, 1);
+    const R d0 = prod_diag_im(x, y, 0), d1 = prod_diag_im(x, y, 1), d2 = prod_diag_im(x, y, 2);
+    o[0] = R(0.5) * (p01.im + p10.im);
+    o[1] = R(0.5) * (p01.re - p10.re);
+    o[2] = R(0.5) * (d0 - d1);
+    o[3] = R(0.5) * (p02.im + p20.im);
+    o[4] = R(0.5) * (p02.re - p20.re);
+    o[5] = R(0.5) * (p12.im + p21.im);
+    o[6] = R(0.5) * (p12.re - p21.re);
+    o[7] = (d0 + d1 - R(2) * d2) * R(0.28867513459481288225);
+  }
   // hermitian H = sum_a v^a lambda^a / 2
   GL_HD static M herm(const R* v) {
     const R r3 = R(0.57735026918962576451);  // 1/sqrt 3

@@ -503,3 +503,85 @@ def test_vacuum_stays_vacuum():
     assert np.all(st.E == 0) and np.all(st.QA == 0)
     s2 = O.step(st, 6)
     assert np.max(np.abs(s2.U - st.U)) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# P12: the improved (semi-implicit) scheme
+# ---------------------------------------------------------------------------
+
+def test_implicit_with_leapfrog_weights_is_leapfrog_bit_for_bit():
+    st = _small_state(3)
+    a = O.step(st, 4)
+    b = O.step_implicit(st, 4, w=(0.0, 1.0, 0.0))
+    assert np.array_equal(a.U, b.U) and np.array_equal(a.E, b.E)
+    assert np.array_equal(a.QA, b.QA) and np.array_equal(a.QB, b.QB)
+
+
+@pytest.mark.parametrize("case", ["kz_polx", "kx_polz", "kxkz_poly"])
+def test_implicit_dispersion_closed_form(case):
+    """Abelian plane waves under the semi-implicit scheme: the time-averaged
+    transverse terms give (a_{n+1} + a_{n-1}) / (2 a_n) =
+    (1 - dt^2 K_z/2 - dt^2 K_T/4) / (1 + dt^2 K_T/4), i.e.
+    (2/dt)^2 sin^2(w dt/2) = K_z + cos^2(w dt/2) K_T; at dt = a_z and
+    k_T = 0 this is w = k_z exactly (no dispersion along z)."""
+    a_z = dt = 0.5
+    p = O.Params(nc=2, nz=40, nx=16, ny=4, a_z=a_z, dt=dt, sigma_l=1.0)
+    Z, Y, X = _grid(p)
+    eps = 1e-5
+    kx = 2 * np.pi * 3 / p.nx
+    kz = 0.7
+    phi = np.zeros((3,) + Z.shape)
+    if case == "kz_polx":
+        pol, KT, Kz = 0, 0.0, (4 / a_z ** 2) * math.sin(kz / 2) ** 2
+        phi[0] = eps * np.cos(kz * Z)
+    elif case == "kx_polz":
+        pol, KT, Kz = 2, 4 * math.sin(kx / 2) ** 2, 0.0
+        phi[2] = eps * np.cos(kx * X)
+    else:
+        pol, KT, Kz = 1, 4 * math.sin(kx / 2) ** 2, (4 / a_z ** 2) * math.sin(kz / 2) ** 2
+        phi[1] = eps * np.cos(kx * X + kz * Z)
+    phi[2][p.nz - 1] = 0.0
+    st = _abelian_state(p, phi, 0.0)
+    s1 = O.step_implicit(st, 1)
+    s2 = O.step_implicit(s1, 1)
+    f0, f1, f2 = (_angle(s.U[pol]) for s in (st, s1, s2))
+    expect = (1 - dt * dt * Kz / 2 - dt * dt * KT / 4) / (1 + dt * dt * KT / 4)
+    inner = (Z >= 5) & (Z <= p.nz - 7) & (np.abs(f1) > 0.1 * eps)
+    assert np.count_nonzero(inner) > 50
+    est = (f2[inner] + f0[inner]) / (2 * f1[inner])
+    assert np.max(np.abs(est - expect)) < 1e-9
+    if case == "kz_polx":
+        assert abs(expect - math.cos(kz)) < 1e-14      # w dt = k_z a_z
+    # phase velocity along z never below 1: w >= k_z for every mode
+    w = math.acos(expect) / dt
+    assert w >= (kz / a_z if case != "kx_polz" else 0.0) - 1e-12
+
+
+def test_implicit_abelian_gauss_is_conserved():
+    """In the U(1) embedding each plane keeps one antisymmetric, time-averaged
+    field strength, so the abelian Gauss law is conserved exactly."""
+    p = O.Params(nc=2, nz=12, nx=6, ny=5, a_z=0.5, dt=0.25)
+    rng = np.random.default_rng(12)
+    phi = 1e-3 * rng.standard_normal((3, p.nz, p.ny, p.nx))
+    phi[2][p.nz - 1] = 0.0
+    e3 = 1e-3 * rng.standard_normal((3, p.nz, p.ny, p.nx))
+    e3[2][p.nz - 1] = 0.0
+    st = _abelian_state(p, phi, e3)
+    st.U_prev = st.U.copy()
+    g0 = O.gauss_divergence(st.U, st.E, p)
+    s = O.step_implicit(st, 6)
+    g1 = O.gauss_divergence(s.U, s.E, p)
+    assert np.max(np.abs(g1 - g0)) < 1e-14
+
+
+def test_implicit_gauss_residual_is_bounded():
+    """Non-abelian collision: the equal-time Gauss residual of the reading
+    adopted is not zero; it stays bounded (reported, not pinned to zero)."""
+    st = _small_state(2, nz=64, nx=6, ny=5, a_z=0.5, dt=0.25, sigma_l=1.5)
+    res = []
+    for _ in range(4):
+        st = O.step_implicit(st, 3)
+        g = O.gauss_residual(st)
+        res.append(g[0] / g[2])
+    assert max(res) < 1e-3
+    assert res[-1] < 3 * max(res[:2])
