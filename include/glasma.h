@@ -107,8 +107,9 @@ typedef struct {
  * stream:   cudaStream_t the context will use (NULL = legacy default).
  * alloc:    NULL for cudaMallocAsync, else the callbacks above.
  * out:      receives the new context (NULL on failure).
- * Errors: INVALID_ARG (nc, sizes, dt > a_z, dt/a_z not a ratio p/q with
- * q <= 4096, nuclei not inside the box), OOM, CUDA, INTERNAL.
+ * Errors: INVALID_ARG (nc, sizes: nz in [2, 65535], nx, ny >= 1 and at
+ * most 1.5e9 sites; dt > a_z, dt/a_z not a ratio p/q with q <= 4096,
+ * nuclei not inside the box), OOM, CUDA, INTERNAL.
  */
 GLASMA_API int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
                    const glasma_allocator* alloc, glasma_ctx** out);

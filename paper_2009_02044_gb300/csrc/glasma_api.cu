@@ -100,6 +100,7 @@ static int check_params(const glasma_params* p) {
   if (p->nc != 2 && p->nc != 3) return set_error(GLASMA_ERR_INVALID_ARG, "nc must be 2 or 3");
   if (p->nz < 2 || p->nx < 1 || p->ny < 1) return set_error(GLASMA_ERR_INVALID_ARG, "need nz >= 2, nx, ny >= 1");
   if ((double)p->nz * p->nx * p->ny > 1.5e9) return set_error(GLASMA_ERR_INVALID_ARG, "lattice too large");
+  if (p->nz > 65535) return set_error(GLASMA_ERR_INVALID_ARG, "nz must be <= 65535 (one grid row per slice)");
   if (!(p->a_t > 0) || !(p->a_z > 0) || !(p->dt > 0))
     return set_error(GLASMA_ERR_INVALID_ARG, "a_t, a_z, dt must be positive");
   if (p->dt > p->a_z) return set_error(GLASMA_ERR_INVALID_ARG, "dt > a_z: a charge would cross several cells");

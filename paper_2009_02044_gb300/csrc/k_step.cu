@@ -31,10 +31,11 @@ struct StepArgs {
   int zA0, WA, zB0, WB;
 };
 
-// One thread per link: the block index interleaves the three directions
-// (i = blockIdx.x % 3) so the blocks working on one region of the lattice
-// run together and share its links in L2; a thread holds one link, the
-// staple sum and one neighbour product at a time.
+// One thread per link: blockIdx.y is the z slice and blockIdx.x interleaves
+// the three directions (i = blockIdx.x % 3) over the transverse plane, so
+// the blocks working on one region of the lattice run together and share
+// its links in L2; a thread holds one link, the staple sum and one
+// neighbour product at a time.
 // FP32 fits 128 registers (4 blocks of 128 threads per SM); FP64 needs
 // twice the registers for the same matrices.
 template <typename R> struct StepOcc { static constexpr int blocks = 4; };
@@ -46,10 +47,12 @@ __global__ void __launch_bounds__(128, StepOcc<R>::blocks) k_step_leapfrog(StepA
   typedef typename G::M M;
   constexpr int NA = G::NA;
   const int i = (int)(blockIdx.x % 3u);
-  const int64_t s = (int64_t)(blockIdx.x / 3u) * blockDim.x + threadIdx.x;
-  if (s >= a.g.V) return;
-  SiteNbr n = site_nbr(a.g, s);
-  if (i == 2 && n.iz == a.g.nz - 1) return;  // no z link on the last slice
+  const uint32_t t = (blockIdx.x / 3u) * blockDim.x + threadIdx.x;  // transverse index
+  const int iz = (int)blockIdx.y;
+  if (t >= (uint32_t)a.g.nxy) return;
+  if (i == 2 && iz == a.g.nz - 1) return;  // no z link on the last slice
+  const SiteNbr n = site_nbr_tz(a.g, t, iz);
+  const int64_t s = n.s;
   const M Ui = LinkIO<NC, R>::template load<R>(a.U, i, a.g.V, s);
   R F[NA];
   link_force_staple<NC, R, R>(a.U, a.g, n, Ui, i, a.w, F);
@@ -57,7 +60,6 @@ __global__ void __launch_bounds__(128, StepOcc<R>::blocks) k_step_leapfrog(StepA
 #pragma unroll
   for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s] + a.dt * F[c];
   if (i == 2 && a.hop) {
-    const int64_t t = s % a.g.nxy;
     R dj[NA];
 #pragma unroll
     for (int c = 0; c < NA; ++c) dj[c] = R(0);
@@ -114,8 +116,8 @@ static int launch_t(glasma_ctx* c, bool hop) {
   a.zB0 = c->zB0;
   a.WB = c->WB;
   const int bs = 128;
-  const int64_t nb = (c->g.V + bs - 1) / bs;
-  k_step_leapfrog<NC, R><<<(unsigned)(3 * nb), bs, 0, c->stream>>>(a);
+  const unsigned ntb = (unsigned)((c->g.nxy + bs - 1) / bs);
+  k_step_leapfrog<NC, R><<<dim3(3 * ntb, (unsigned)c->g.nz), bs, 0, c->stream>>>(a);
   return cuda_check(cudaGetLastError(), "k_step_leapfrog launch");
 }
 

@@ -108,6 +108,28 @@ GL_HD SiteNbr site_nbr(const Geom& g, int64_t s) {
   return n;
 }
 
+// The same from the transverse index t = iy*nx + ix (< 2^31) and the slice
+// iz, with 32-bit division only.
+GL_HD SiteNbr site_nbr_tz(const Geom& g, uint32_t t, int iz) {
+  SiteNbr n;
+  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+  const uint32_t iy = t / nx, ix = t - iy * nx;
+  n.ix = (int)ix;
+  n.iy = (int)iy;
+  n.iz = iz;
+  const int64_t base = (int64_t)iz * g.nxy;
+  n.s = base + t;
+  const uint32_t xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+  const uint32_t yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+  n.p[0] = base + iy * nx + xp;
+  n.m[0] = base + iy * nx + xm;
+  n.p[1] = base + yp * nx + ix;
+  n.m[1] = base + ym * nx + ix;
+  n.p[2] = n.s + g.nxy;
+  n.m[2] = n.s - g.nxy;
+  return n;
+}
+
 // Index of x + e_i - e_j for i != j.
 GL_HD int64_t diag_pm(const Geom& g, const SiteNbr& n, int i, int j) {
   int d[3] = {0, 0, 0};
