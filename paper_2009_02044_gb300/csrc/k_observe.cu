@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
     const int ilast = (iz == a.g.nz - 1) ? 2 : 3;
     for (int i = 0; i < ilast; ++i) {
       R F[NA];
-      link_force_staple<NC, R, R>(a.U, a.g, n, Uo[i], i, a.w, F);
+      link_force_staple<NC, R, R>(a.U, a.g, n, i, a.w, F);
       R en[NA], eo[NA];
 #pragma unroll
       for (int c = 0; c < NA; ++c) {

@@ -31,31 +31,30 @@ struct StepArgs {
   int zA0, WA, zB0, WB;
 };
 
-// One thread per link: blockIdx.y is the z slice and blockIdx.x interleaves
-// the three directions (i = blockIdx.x % 3) over the transverse plane, so
-// the blocks working on one region of the lattice run together and share
-// its links in L2; a thread holds one link, the staple sum and one
-// neighbour product at a time.
-// FP32 fits 128 registers (4 blocks of 128 threads per SM); FP64 needs
-// twice the registers for the same matrices.
-template <typename R> struct StepOcc { static constexpr int blocks = 4; };
-template <> struct StepOcc<double> { static constexpr int blocks = 2; };
+// One thread per link.  A block is 64 consecutive transverse sites times the
+// three directions (threadIdx.y = direction), so the three link updates of a
+// site run together and share the neighbour links in L1; blockIdx.y is the
+// z slice.  A thread holds the staple sum and one neighbour product at a
+// time and reloads its own link after the staples (fewer live registers).
+// FP32: 3 blocks of 192 threads per SM; FP64 needs twice the registers.
+template <typename R> struct StepOcc { static constexpr int blocks = 3; };
+template <> struct StepOcc<double> { static constexpr int blocks = 1; };
 
 template <int NC, typename R>
-__global__ void __launch_bounds__(128, StepOcc<R>::blocks) k_step_leapfrog(StepArgs<R> a) {
+__global__ void __launch_bounds__(192, StepOcc<R>::blocks) k_step_leapfrog(StepArgs<R> a) {
   typedef Group<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  const int i = (int)(blockIdx.x % 3u);
-  const uint32_t t = (blockIdx.x / 3u) * blockDim.x + threadIdx.x;  // transverse index
+  const int i = (int)threadIdx.y;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // transverse index
   const int iz = (int)blockIdx.y;
   if (t >= (uint32_t)a.g.nxy) return;
   if (i == 2 && iz == a.g.nz - 1) return;  // no z link on the last slice
   const SiteNbr n = site_nbr_tz(a.g, t, iz);
   const int64_t s = n.s;
-  const M Ui = LinkIO<NC, R>::template load<R>(a.U, i, a.g.V, s);
   R F[NA];
-  link_force_staple<NC, R, R>(a.U, a.g, n, Ui, i, a.w, F);
+  link_force_staple<NC, R, R>(a.U, a.g, n, i, a.w, F);
+  const M Ui = LinkIO<NC, R>::template load<R>(a.U, i, a.g.V, s);
   R e[NA];
 #pragma unroll
   for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s] + a.dt * F[c];
@@ -115,9 +114,9 @@ static int launch_t(glasma_ctx* c, bool hop) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
-  const int bs = 128;
+  const int bs = 64;
   const unsigned ntb = (unsigned)((c->g.nxy + bs - 1) / bs);
-  k_step_leapfrog<NC, R><<<dim3(3 * ntb, (unsigned)c->g.nz), bs, 0, c->stream>>>(a);
+  k_step_leapfrog<NC, R><<<dim3(ntb, (unsigned)c->g.nz), dim3(bs, 3), 0, c->stream>>>(a);
   return cuda_check(cudaGetLastError(), "k_step_leapfrog launch");
 }
 

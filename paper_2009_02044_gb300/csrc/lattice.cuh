@@ -147,8 +147,8 @@ GL_HD int64_t diag_pm(const Geom& g, const SiteNbr& n, int i, int j) {
 // since Im tr t^a (U_i S) is linear in S.  Only the anti-hermitian part of
 // the last product is formed.
 template <int NC, typename Rs, typename Rc>
-GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const SiteNbr& n,
-                             const typename Group<NC, Rc>::M& Ui, int i, const Rc* w, Rc* F) {
+GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const SiteNbr& n, int i, const Rc* w,
+                             Rc* F) {
   typedef Group<NC, Rc> G;
   typedef typename G::M M;
   M S = G::zero();
@@ -172,7 +172,8 @@ GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const 
   }
   constexpr int NA = G::NA;
   Rc pr[NA];
-  G::proj_mul(Ui, S, pr);
+  // U_i(x) is loaded only here, so it is not live across the staples
+  G::proj_mul(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.s), S, pr);
 #pragma unroll
   for (int a = 0; a < NA; ++a) F[a] = -pr[a];
 }

@@ -314,6 +314,20 @@ struct Group<3, R> {
     M Q2 = mul(Q, Q);
     R c1 = R(0.5) * (Q2.m[0].re + Q2.m[4].re + Q2.m[8].re);
     if (c1 == R(0)) return ident();
+    // Small arguments: the series 1 + iQ - Q^2/2 is exact to rounding (its
+    // truncation |Q|^3/6 is below the unit roundoff), and the eigenvalue
+    // parametrisation below would underflow (c0max = 2 (c1/3)^{3/2} -> 0).
+    const R small = sizeof(R) == 4 ? R(1e-8) : R(1e-20);
+    if (c1 < small) {
+      M r;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        cplx<R> acc{-R(0.5) * Q2.m[k].re - Q.m[k].im, -R(0.5) * Q2.m[k].im + Q.m[k].re};
+        if (k % 4 == 0) acc.re += R(1);
+        r.m[k] = acc;
+      }
+      return r;
+    }
     // det of the hermitian Q (real)
     cplx<R> d = Q.m[0] * (Q.m[4] * Q.m[8] - Q.m[5] * Q.m[7]) -
                 Q.m[1] * (Q.m[3] * Q.m[8] - Q.m[5] * Q.m[6]) +

@@ -1,0 +1,51 @@
+"""The benchmark's multi-rank path (replicas, one event per rank) on CPU:
+two gloo ranks agree on the slowest rank's time and on the aggregate
+throughput."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms_local = [12.0, 20.0][rank]
+    ms_max, value = bench.aggregate(ms_local, 1000, 50, world)
+    q.put((rank, ms_max, value))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_replicas():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms_max, value in res:
+        assert ms_max == 20.0
+        assert value == pytest.approx(2 * 1000 * 50 / 0.020)
+
+
+def test_single_rank_aggregate():
+    import bench
+    ms, v = bench.aggregate(10.0, 100, 10, 1)
+    assert ms == 10.0 and v == pytest.approx(100 * 10 / 0.010)
