@@ -97,13 +97,15 @@ __device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R*
 
 // U(t_{n-1}) = exp(-i dt E(t_{n-1/2})) U(t_n), when it is not known.
 template <int NC, typename R>
-__global__ void __launch_bounds__(128) k_implicit_prev(ImplArgs<R> a) {
+__global__ void __launch_bounds__(192) k_implicit_prev(ImplArgs<R> a) {
   typedef Group<NC, R> G;
   constexpr int NA = G::NA;
-  const int i = blockIdx.y;
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.g.V) return;
-  if (i == 2 && (int)(s / a.g.nxy) == a.g.nz - 1) return;
+  const int i = (int)threadIdx.y;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iz = (int)blockIdx.y;
+  if (t >= (uint32_t)a.g.nxy) return;
+  if (i == 2 && iz == a.g.nz - 1) return;
+  const int64_t s = (int64_t)iz * a.g.nxy + t;
   R e[NA];
 #pragma unroll
   for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
@@ -114,21 +116,21 @@ __global__ void __launch_bounds__(128) k_implicit_prev(ImplArgs<R> a) {
 
 // Hop (charges committed, current into Ework) and the first iterate.
 template <int NC, typename R>
-__global__ void __launch_bounds__(128) k_implicit_prep(ImplArgs<R> a) {
+__global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
   typedef Group<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  const int i = blockIdx.y;
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.g.V) return;
-  const int iz = (int)(s / a.g.nxy);
+  const int i = (int)threadIdx.y;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iz = (int)blockIdx.y;
+  if (t >= (uint32_t)a.g.nxy) return;
   if (i == 2 && iz == a.g.nz - 1) return;
+  const int64_t s = (int64_t)iz * a.g.nxy + t;
   const M Ui = LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s);
   R e[NA], ew[NA];
 #pragma unroll
   for (int c = 0; c < NA; ++c) ew[c] = e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
   if (i == 2 && a.hop) {
-    const int64_t t = s % a.g.nxy;
     const int kb = iz - a.zB0;
     R dj[NA];
 #pragma unroll
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(128) k_implicit_prep(ImplArgs<R> a) {
 
 // One fixed-point sweep: E = Ework + dt F(U_{n-1}, U_n, X), Xn = exp(i dt E) U_n.
 template <int NC, typename R>
-__global__ void __launch_bounds__(128, 2) k_implicit_iter(ImplArgs<R> a) {
+__global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
   typedef Group<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
@@ -175,13 +177,15 @@ __global__ void __launch_bounds__(128, 2) k_implicit_iter(ImplArgs<R> a) {
   // rounding floor of the state's precision)
   if (a.k > 0 && a.conv[a.k - 1] < a.tol) return;
   if (a.k > 1 && a.conv[a.k - 1] >= a.conv[a.k - 2]) return;
-  __shared__ double smax[128];
-  const int i = blockIdx.y;
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double smax[6];
+  const int i = (int)threadIdx.y;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iz = (int)blockIdx.y;
   double dmax = 0.0;
-  const bool live = s < a.g.V && !(i == 2 && (int)(s / a.g.nxy) == a.g.nz - 1);
+  const bool live = t < (uint32_t)a.g.nxy && !(i == 2 && iz == a.g.nz - 1);
   if (live) {
-    SiteNbr n = site_nbr(a.g, s);
+    const SiteNbr n = site_nbr_tz(a.g, t, iz);
+    const int64_t s = n.s;
     R F[NA];
     force_implicit<NC, R>(a, n, i, F);
     R e[NA];
@@ -197,14 +201,17 @@ __global__ void __launch_bounds__(128, 2) k_implicit_iter(ImplArgs<R> a) {
     if (sizeof(R) == 4) u = G::reunit(u);
     LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
   }
-  smax[threadIdx.x] = dmax;
+  // block max: warp shuffles, then one value per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31, warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if (lane == 0) smax[warp] = dmax;
   __syncthreads();
-  for (int w = 64; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
-    __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double m = smax[0];
+    for (int w = 1; w < (int)(blockDim.x * blockDim.y) / 32; ++w) m = fmax(m, smax[w]);
+    atomicMax((unsigned long long*)&a.conv[a.k], (unsigned long long)__double_as_longlong(m));
   }
-  if (threadIdx.x == 0)
-    atomicMax((unsigned long long*)&a.conv[a.k], (unsigned long long)__double_as_longlong(smax[0]));
 }
 
 template <int NC, typename R>
@@ -234,8 +241,10 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   void* xb = c->Uit;
   a.Up = (const V2*)prev;
   a.Un = (const V2*)now;
-  const int bs = 128;
-  const dim3 grid((unsigned)((c->g.V + bs - 1) / bs), 3);
+  // 64 transverse sites x the three directions per block, one row of
+  // blocks per z slice (the directions share neighbour links in L1)
+  const dim3 bs(64, 3);
+  const dim3 grid((unsigned)((c->g.nxy + 63) / 64), (unsigned)c->g.nz);
   int st;
   if (!c->uprev_valid) {
     a.Uout = (V2*)prev;
