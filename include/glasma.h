@@ -175,6 +175,8 @@ GLASMA_API int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total);
  *   U  links, complex component k of link d at U[(d*NV + k)*V + s] as
  *      (re, im) pairs of R; SU(2): NV = 2, (alpha, beta) of
  *      [[alpha, beta], [-beta*, alpha*]]; SU(3): NV = 9, row-major 3x3;
+ *      in FP32 the stored matrix is U - 1 (alpha - 1 for SU(2)), in FP64
+ *      it is U;
  *   E  fields, E[(d*(nc^2-1) + a)*V + s];
  *   QA, QB charge windows of zA0.. zA0+WA-1 and zB0.. zB0+WB-1 (z slices),
  *      Q[(a*W + w)*nx*ny + t]; a pointer may be NULL when its W is 0.

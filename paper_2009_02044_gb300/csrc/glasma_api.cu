@@ -290,13 +290,19 @@ int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total) {
 // fields in FP64 (host marshalling of the device layout)
 // ---------------------------------------------------------------------------
 
+// FP32 storage holds U - 1 (deviation form, see link_alg.cuh): the
+// identity is added on the way out and removed (in FP64) on the way in.
 static void link_to_matrix(const glasma_ctx* c, const double* comp, double* m) {
   // comp: NV complex (re, im); m: nc x nc complex (re, im)
+  const double one = c->rs == 4 ? 1.0 : 0.0;
   if (c->p.nc == 3) {
     memcpy(m, comp, sizeof(double) * 18);
+    m[0] += one;
+    m[8] += one;
+    m[16] += one;
     return;
   }
-  const double ar = comp[0], ai = comp[1], br = comp[2], bi = comp[3];
+  const double ar = comp[0] + one, ai = comp[1], br = comp[2], bi = comp[3];
   m[0] = ar;  m[1] = ai;   // alpha
   m[2] = br;  m[3] = bi;   // beta
   m[4] = -br; m[5] = bi;   // -conj(beta)
@@ -304,11 +310,15 @@ static void link_to_matrix(const glasma_ctx* c, const double* comp, double* m) {
 }
 
 static void matrix_to_link(const glasma_ctx* c, const double* m, double* comp) {
+  const double one = c->rs == 4 ? 1.0 : 0.0;
   if (c->p.nc == 3) {
     memcpy(comp, m, sizeof(double) * 18);
+    comp[0] -= one;
+    comp[8] -= one;
+    comp[16] -= one;
     return;
   }
-  comp[0] = m[0];
+  comp[0] = m[0] - one;
   comp[1] = m[1];
   comp[2] = m[2];
   comp[3] = m[3];

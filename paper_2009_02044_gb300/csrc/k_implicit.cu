@@ -58,7 +58,7 @@ __device__ __forceinline__ const typename V2T<R>::T* slot_buf(const ImplArgs<R>&
 // Time-averaged force on link i at x.
 template <int NC, typename R>
 __device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R* F) {
-  typedef Group<NC, R> G;
+  typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
   const R wt[3] = {R(0.25), R(0.5), R(0.25)};
@@ -74,21 +74,21 @@ __device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R*
     for (int m = 0; m < 3; ++m) {
       const typename V2T<R>::T* Bi = slot_buf(a, m, zplane, i);
       const typename V2T<R>::T* Bj = slot_buf(a, m, zplane, j);
-      M S = G::zero();
+      typename G::Sum S = G::zero_sum();
       if (fwd) {
         M T = G::mul_d(LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.p[i]),
                        LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.p[j]));
         T = G::mul_d(T, LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.s));
-        G::scale_add(S, R(1), T);
+        G::sum_add(S, R(1), T);
       }
       if (bwd) {
         M T = G::mul(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.m[j]),
                      LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, diag_pm(a.g, n, i, j)));
         T = G::d_mul(T, LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.m[j]));
-        G::scale_add(S, R(1), T);
+        G::sum_add(S, R(1), T);
       }
       R pr[NA];
-      G::proj_mul(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.s), S, pr);
+      G::proj_mul_sum(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.s), S, pr);
 #pragma unroll
       for (int c = 0; c < NA; ++c) F[c] -= a.w[j] * wt[m] * pr[c];
     }
@@ -98,7 +98,7 @@ __device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R*
 // U(t_{n-1}) = exp(-i dt E(t_{n-1/2})) U(t_n), when it is not known.
 template <int NC, typename R>
 __global__ void __launch_bounds__(192) k_implicit_prev(ImplArgs<R> a) {
-  typedef Group<NC, R> G;
+  typedef LinkAlg<NC, R> G;
   constexpr int NA = G::NA;
   const int i = (int)threadIdx.y;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(192) k_implicit_prev(ImplArgs<R> a) {
 // Hop (charges committed, current into Ework) and the first iterate.
 template <int NC, typename R>
 __global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
-  typedef Group<NC, R> G;
+  typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
   const int i = (int)threadIdx.y;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
 // One fixed-point sweep: E = Ework + dt F(U_{n-1}, U_n, X), Xn = exp(i dt E) U_n.
 template <int NC, typename R>
 __global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
-  typedef Group<NC, R> G;
+  typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
   // converged earlier: below the tolerance, or no longer decreasing (the

@@ -189,7 +189,7 @@ struct TmnArgs {
 // the step kernel would write), every accumulation in FP64.
 template <int NC, typename R>
 __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
-  typedef Group<NC, R> G;
+  typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
   __shared__ double sh[5][kRedThreads];

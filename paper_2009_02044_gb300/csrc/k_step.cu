@@ -42,7 +42,7 @@ template <> struct StepOcc<double> { static constexpr int blocks = 1; };
 
 template <int NC, typename R>
 __global__ void __launch_bounds__(192, StepOcc<R>::blocks) k_step_leapfrog(StepArgs<R> a) {
-  typedef Group<NC, R> G;
+  typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
   const int i = (int)threadIdx.y;

@@ -13,7 +13,7 @@
 #pragma once
 #include <stdint.h>
 
-#include "su_n.cuh"
+#include "link_alg.cuh"
 
 namespace glasma {
 
@@ -42,18 +42,29 @@ GL_HD int64_t shifted(const Geom& g, int ix, int iy, int iz, int dx, int dy, int
 
 template <int NC, typename R> struct LinkIO;
 
+// FP32 storage holds U - 1 (see link_alg.cuh); loading it as FP64 gives the
+// full matrix, storing an FP64 full matrix into it subtracts the identity
+// before rounding.  FP64 storage holds U.
+template <typename Rs, typename Rc>
+struct DeltaConv {
+  static constexpr bool to_full = sizeof(Rs) == 4 && sizeof(Rc) == 8;
+};
+
 template <typename R>
 struct LinkIO<2, R> {
   template <typename Rc>
   GL_HD static typename Group<2, Rc>::M load(const typename V2T<R>::T* U, int d, int64_t V, int64_t s) {
     typename V2T<R>::T a = U[(int64_t)(d * 2 + 0) * V + s];
     typename V2T<R>::T b = U[(int64_t)(d * 2 + 1) * V + s];
-    return typename Group<2, Rc>::M{{Rc(a.x), Rc(a.y)}, {Rc(b.x), Rc(b.y)}};
+    typename Group<2, Rc>::M m{{Rc(a.x), Rc(a.y)}, {Rc(b.x), Rc(b.y)}};
+    if (DeltaConv<R, Rc>::to_full) m.a.re += Rc(1);
+    return m;
   }
   template <typename Rc>
   GL_HD static void store(typename V2T<R>::T* U, int d, int64_t V, int64_t s, const typename Group<2, Rc>::M& m) {
     typename V2T<R>::T a, b;
-    a.x = R(m.a.re); a.y = R(m.a.im);
+    const Rc one = DeltaConv<R, Rc>::to_full ? Rc(1) : Rc(0);
+    a.x = R(m.a.re - one); a.y = R(m.a.im);
     b.x = R(m.b.re); b.y = R(m.b.im);
     U[(int64_t)(d * 2 + 0) * V + s] = a;
     U[(int64_t)(d * 2 + 1) * V + s] = b;
@@ -70,14 +81,20 @@ struct LinkIO<3, R> {
       typename V2T<R>::T v = U[(int64_t)(d * 9 + k) * V + s];
       m.m[k] = cplx<Rc>{Rc(v.x), Rc(v.y)};
     }
+    if (DeltaConv<R, Rc>::to_full) {
+      m.m[0].re += Rc(1);
+      m.m[4].re += Rc(1);
+      m.m[8].re += Rc(1);
+    }
     return m;
   }
   template <typename Rc>
   GL_HD static void store(typename V2T<R>::T* U, int d, int64_t V, int64_t s, const typename Group<3, Rc>::M& m) {
+    const Rc one = DeltaConv<R, Rc>::to_full ? Rc(1) : Rc(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       typename V2T<R>::T v;
-      v.x = R(m.m[k].re);
+      v.x = R(k % 4 == 0 ? m.m[k].re - one : m.m[k].re);
       v.y = R(m.m[k].im);
       U[(int64_t)(d * 9 + k) * V + s] = v;
     }
@@ -149,9 +166,9 @@ GL_HD int64_t diag_pm(const Geom& g, const SiteNbr& n, int i, int j) {
 template <int NC, typename Rs, typename Rc>
 GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const SiteNbr& n, int i, const Rc* w,
                              Rc* F) {
-  typedef Group<NC, Rc> G;
+  typedef LinkAlg<NC, Rc> G;
   typedef typename G::M M;
-  M S = G::zero();
+  typename G::Sum S = G::zero_sum();
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     if (j == i) continue;
@@ -161,19 +178,19 @@ GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const 
       M T = G::mul_d(LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.p[i]),
                      LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.p[j]));
       T = G::mul_d(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.s));
-      G::scale_add(S, w[j], T);
+      G::sum_add(S, w[j], T);
     }
     if (bwd) {
       M T = G::mul(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.m[j]),
                    LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, diag_pm(g, n, i, j)));
       T = G::d_mul(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.m[j]));
-      G::scale_add(S, w[j], T);
+      G::sum_add(S, w[j], T);
     }
   }
   constexpr int NA = G::NA;
   Rc pr[NA];
   // U_i(x) is loaded only here, so it is not live across the staples
-  G::proj_mul(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.s), S, pr);
+  G::proj_mul_sum(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.s), S, pr);
 #pragma unroll
   for (int a = 0; a < NA; ++a) F[a] = -pr[a];
 }

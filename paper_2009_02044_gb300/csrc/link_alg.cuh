@@ -1,0 +1,328 @@
+// Arithmetic on stored links.
+//
+// FP64 links are stored and multiplied as full matrices (Group<NC, double>).
+// FP32 links are stored and multiplied as their deviation from the identity,
+// d = U - 1.  Links near the identity (weak fields, vacuum, and the slowly
+// varying pure-gauge links of the nuclei, |U - 1| <~ 0.1) then carry
+// rounding errors of the size u |d| instead of u, in storage and in every
+// product, so the force -- a small anti-hermitian difference of O(1)
+// products -- keeps about log10(1/|d|) more digits in FP32.
+//
+// Interface shared by both representations (M = a stored-form link):
+//   ident, mul, mul_d (x y^+), d_mul (x^+ y)       products of links
+//   Sum, zero_sum, sum_add                          weighted staple sums
+//   proj_mul(u, S)                                  Im tr t^a (U S)
+//   expi(v, c)                                      exp(i c v^a t^a)
+//   reunit, adj (U q U^+), adj_dag (U^+ q U)
+#pragma once
+#include "su_n.cuh"
+
+namespace glasma {
+
+template <int NC, typename R> struct LinkAlg;
+
+// ---------------------------------------------------------------------------
+// Full matrices (FP64 state).
+// ---------------------------------------------------------------------------
+template <int NC>
+struct LinkAlg<NC, double> : Group<NC, double> {
+  typedef Group<NC, double> G;
+  typedef typename G::M M;
+  static constexpr bool kDelta = false;
+  typedef M Sum;
+  GL_HD static M full(const M& u) { return u; }
+  GL_HD static Sum zero_sum() { return G::zero(); }
+  GL_HD static void sum_add(Sum& s, double w, const M& t) { G::scale_add(s, w, t); }
+  GL_HD static void proj_mul_sum(const M& u, const Sum& s, double* out) { G::proj_mul(u, s, out); }
+};
+
+// ---------------------------------------------------------------------------
+// SU(3), FP32, deviation form: M holds d = U - 1 (row major).
+// ---------------------------------------------------------------------------
+template <>
+struct LinkAlg<3, float> {
+  typedef float R;
+  typedef Group<3, float> G;
+  typedef G::M M;
+  static constexpr int NA = 8;
+  static constexpr bool kDelta = true;
+
+  GL_HD static M ident() { return G::zero(); }
+  GL_HD static M full(const M& d) {
+    M u = d;
+    u.m[0].re += 1.f;
+    u.m[4].re += 1.f;
+    u.m[8].re += 1.f;
+    return u;
+  }
+  // (1+x)(1+y) - 1 = x (1+y) + y: the products carry the small factor x,
+  // so their rounding stays of the size u |x| even though 1+y is O(1).
+  GL_HD static M mul(const M& x, const M& y) {
+    const M y1 = full(y);
+    M r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        cplx<R> acc = fma_c(x.m[3 * i], y1.m[j], y.m[3 * i + j]);
+        acc = fma_c(x.m[3 * i + 1], y1.m[3 + j], acc);
+        acc = fma_c(x.m[3 * i + 2], y1.m[6 + j], acc);
+        r.m[3 * i + j] = acc;
+      }
+    return r;
+  }
+  // (1+x)(1+y)^+ - 1 = x (1+y)^+ + y^+
+  GL_HD static M mul_d(const M& x, const M& y) {
+    const M y1 = full(y);
+    M r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        cplx<R> acc = cj(y.m[3 * j + i]);
+        acc = acc + mulc(x.m[3 * i], y1.m[3 * j]);
+        acc = acc + mulc(x.m[3 * i + 1], y1.m[3 * j + 1]);
+        acc = acc + mulc(x.m[3 * i + 2], y1.m[3 * j + 2]);
+        r.m[3 * i + j] = acc;
+      }
+    return r;
+  }
+  // (1+x)^+(1+y) - 1 = (1+x)^+ y + x^+
+  GL_HD static M d_mul(const M& x, const M& y) {
+    const M x1 = full(x);
+    M r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        cplx<R> acc = cj(x.m[3 * j + i]);
+        acc = acc + mulc(y.m[j], x1.m[i]);
+        acc = acc + mulc(y.m[3 + j], x1.m[3 + i]);
+        acc = acc + mulc(y.m[6 + j], x1.m[6 + i]);
+        r.m[3 * i + j] = acc;
+      }
+    return r;
+  }
+
+  // Staple sums c 1 + d (d a full matrix, c the summed weights).
+  struct Sum {
+    R c;
+    M d;
+  };
+  GL_HD static Sum zero_sum() { return Sum{0.f, G::zero()}; }
+  GL_HD static void sum_add(Sum& s, R w, const M& t) {
+    s.c += w;
+    G::scale_add(s.d, w, t);
+  }
+  // Im tr t^a (1+u)(c + d) = Im tr t^a (d + u (c + d)): the identity part
+  // projects to zero; only the anti-hermitian part of d + u (c + d) is formed.
+  GL_HD static void proj_mul_sum(const M& u, const Sum& s, R* o) {
+    M d1 = s.d;
+    d1.m[0].re += s.c;
+    d1.m[4].re += s.c;
+    d1.m[8].re += s.c;
+    cplx<R> p[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (i == j) continue;
+        cplx<R> acc = fma_c(u.m[3 * i], d1.m[j], s.d.m[3 * i + j]);
+        acc = fma_c(u.m[3 * i + 1], d1.m[3 + j], acc);
+        p[3 * i + j] = fma_c(u.m[3 * i + 2], d1.m[6 + j], acc);
+      }
+    R dg[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R acc = s.d.m[4 * i].im;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        acc = fma(u.m[3 * i + k].re, d1.m[3 * k + i].im, acc);
+        acc = fma(u.m[3 * i + k].im, d1.m[3 * k + i].re, acc);
+      }
+      dg[i] = acc;
+    }
+    o[0] = 0.5f * (p[1].im + p[3].im);
+    o[1] = 0.5f * (p[1].re - p[3].re);
+    o[2] = 0.5f * (dg[0] - dg[1]);
+    o[3] = 0.5f * (p[2].im + p[6].im);
+    o[4] = 0.5f * (p[2].re - p[6].re);
+    o[5] = 0.5f * (p[5].im + p[7].im);
+    o[6] = 0.5f * (p[5].re - p[7].re);
+    o[7] = (dg[0] + dg[1] - 2.f * dg[2]) * 0.28867513459481288225f;
+  }
+  // Same interface for a plain product (1+u) X with X full.
+  GL_HD static void proj_mul(const M& u, const M& x, R* o) {
+    Sum s{0.f, x};
+    proj_mul_sum(u, s, o);
+  }
+
+  // exp(i c v^a t^a) - 1 without forming the identity: the series
+  // e = iQ (1 + iQ/2 (1 + iQ/3 (1 + iQ/4))) at Q / 2^s with ||Q||_F / 2^s
+  // <= 1/32 (truncation below 1e-8 of |e|), then s exact doublings
+  // e_{2h} = 2 e_h + e_h^2 (from exp(iQ) = exp(iQ/2)^2).
+  GL_HD static M expi(const R* v, R c) {
+    R nq2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) nq2 += v[a] * v[a];
+    R nq = fabsf(c) * gl_sqrt(0.5f * nq2);
+    if (nq == 0.f) return G::zero();
+    int s = 0;
+    R sc = c;
+    while (nq > 0.03125f && s < 40) {
+      nq *= 0.5f;
+      sc *= 0.5f;
+      ++s;
+    }
+    R cv[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) cv[a] = sc * v[a];
+    const M Q = G::herm(cv);
+    // Horner: Y <- 1 + (i/k) Q Y for k = 4, 3, 2, then e = i Q Y
+    M Y;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Y.m[k] = cplx<R>{-0.25f * Q.m[k].im, 0.25f * Q.m[k].re};  // iQ/4
+    Y.m[0].re += 1.f;
+    Y.m[4].re += 1.f;
+    Y.m[8].re += 1.f;
+#pragma unroll
+    for (int k = 3; k >= 2; --k) {
+      const M QY = G::mul(Q, Y);
+      const R f = 1.f / (R)k;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Y.m[q] = cplx<R>{-f * QY.m[q].im, f * QY.m[q].re};
+      Y.m[0].re += 1.f;
+      Y.m[4].re += 1.f;
+      Y.m[8].re += 1.f;
+    }
+    M e = G::mul(Q, Y);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) e.m[q] = cplx<R>{-e.m[q].im, e.m[q].re};  // times i
+    for (int k = 0; k < s; ++k) {
+      const M e2 = G::mul(e, e);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) e.m[q] = (R)2 * e.m[q] + e2.m[q];
+    }
+    return e;
+  }
+
+  // Re-unitarisation of 1 + d: rows 0 and 1 by Gram-Schmidt, row 2 =
+  // conj(row0 x row1), every step written for the deviation from e_k so
+  // that no O(1) quantity is formed.
+  GL_HD static R inv_sqrt_m1(R eps) {  // 1/sqrt(1+eps) - 1
+    const R r = gl_sqrt(1.f + eps);
+    return -eps / (r * (1.f + r));
+  }
+  GL_HD static M reunit(const M& x) {
+    M r;
+    const cplx<R>* a = &x.m[0];
+    R e0 = 2.f * a[0].re;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e0 += a[k].re * a[k].re + a[k].im * a[k].im;
+    const R g0 = inv_sqrt_m1(e0), f0 = 1.f + g0;
+    cplx<R> ap[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ap[k] = f0 * a[k];
+    ap[0].re += g0;
+    // row 1 = e1 + b: p = <row0', row1> = b0 + conj(a'_1) + sum conj(a'_k) b_k
+    const cplx<R>* b = &x.m[3];
+    cplx<R> p = b[0] + cj(ap[1]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p = p + mulc(b[k], ap[k]);
+    cplx<R> bb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bb[k] = b[k] - p * ap[k];
+    bb[0] = bb[0] - p;
+    R e1 = 2.f * bb[1].re;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e1 += bb[k].re * bb[k].re + bb[k].im * bb[k].im;
+    const R g1 = inv_sqrt_m1(e1), f1 = 1.f + g1;
+    cplx<R> bp[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bp[k] = f1 * bb[k];
+    bp[1].re += g1;
+    // row 2 - e2 = conj(e0 x b' + a' x e1 + a' x b')
+    const cplx<R> c0 = ap[1] * bp[2] - ap[2] * bp[1] - ap[2];
+    const cplx<R> c1 = ap[2] * bp[0] - ap[0] * bp[2] - bp[2];
+    const cplx<R> c2 = ap[0] * bp[1] - ap[1] * bp[0] + bp[1] + ap[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r.m[k] = ap[k];
+      r.m[3 + k] = bp[k];
+    }
+    r.m[6] = cj(c0);
+    r.m[7] = cj(c1);
+    r.m[8] = cj(c2);
+    return r;
+  }
+
+  // Adjoint transport of an algebra vector (not a small difference: the full
+  // link is used).
+  GL_HD static void adj(const M& u, R* q) { G::adj(full(u), q); }
+  GL_HD static void adj_dag(const M& u, R* q) { G::adj_dag(full(u), q); }
+};
+
+// ---------------------------------------------------------------------------
+// SU(2), FP32, deviation form: M = (alpha - 1, beta).
+// ---------------------------------------------------------------------------
+template <>
+struct LinkAlg<2, float> {
+  typedef float R;
+  typedef Group<2, float> G;
+  typedef G::M M;
+  static constexpr int NA = 3;
+  static constexpr bool kDelta = true;
+
+  GL_HD static M ident() { return G::zero(); }
+  GL_HD static M full(const M& d) { return M{{d.a.re + 1.f, d.a.im}, d.b}; }
+  GL_HD static M dag(const M& x) { return M{cj(x.a), -x.b}; }
+  // alpha = a1 + a2 + a1 a2 - b1 b2*, beta = b1 + b2 + a1 b2 + b1 a2*
+  GL_HD static M mul(const M& x, const M& y) {
+    return M{x.a + y.a + x.a * y.a - mulc(x.b, y.b), x.b + y.b + x.a * y.b + mulc(x.b, y.a)};
+  }
+  GL_HD static M mul_d(const M& x, const M& y) { return mul(x, dag(y)); }
+  GL_HD static M d_mul(const M& x, const M& y) { return mul(dag(x), y); }
+
+  struct Sum {
+    R c;
+    M d;
+  };
+  GL_HD static Sum zero_sum() { return Sum{0.f, G::zero()}; }
+  GL_HD static void sum_add(Sum& s, R w, const M& t) {
+    s.c += w;
+    G::scale_add(s.d, w, t);
+  }
+  // Im tr t^a (1+u)(c + d) = Im tr t^a (c u + d + u d)
+  GL_HD static void proj_mul_sum(const M& u, const Sum& s, R* o) {
+    M y{s.c * u.a + s.d.a, s.c * u.b + s.d.b};
+    R p[NA], q[NA];
+    G::proj(y, p);
+    G::proj(G::mul(u, s.d), q);
+#pragma unroll
+    for (int k = 0; k < NA; ++k) o[k] = p[k] + q[k];
+  }
+  GL_HD static void proj_mul(const M& u, const M& x, R* o) {
+    Sum s{0.f, x};
+    proj_mul_sum(u, s, o);
+  }
+  // exp(i c v.sigma/2) - 1 = (cos th - 1 + i sin th n3, sin th (n2 + i n1)),
+  // cos th - 1 = -2 sin^2(th/2)
+  GL_HD static M expi(const R* v, R c) {
+    const R n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    if (n2 == 0.f) return G::zero();
+    const R nrm = gl_sqrt(n2);
+    R sh, ch;
+    gl_sincos(0.25f * c * nrm, &sh, &ch);  // half of th = c |v| / 2
+    const R s = 2.f * sh * ch, f = s / nrm;
+    return M{{-2.f * sh * sh, f * v[2]}, {f * v[1], f * v[0]}};
+  }
+  GL_HD static M reunit(const M& x) {
+    const R eps = 2.f * x.a.re + x.a.re * x.a.re + x.a.im * x.a.im + x.b.re * x.b.re + x.b.im * x.b.im;
+    const R r = gl_sqrt(1.f + eps), g = -eps / (r * (1.f + r)), f = 1.f + g;
+    return M{{g + f * x.a.re, f * x.a.im}, f * x.b};
+  }
+  GL_HD static void adj(const M& u, R* q) { G::adj(full(u), q); }
+  GL_HD static void adj_dag(const M& u, R* q) { G::adj_dag(full(u), q); }
+};
+
+}  // namespace glasma

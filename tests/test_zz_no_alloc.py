@@ -40,6 +40,8 @@ def _device_layout(G, h, dtype):
     V = p.nz * p.ny * p.nx
     U, E, QA, QB, n = G.glasma_get_fields(h)
     U = U.reshape(3, V, nc, nc)
+    if dtype == torch.float32:      # FP32 links are stored as U - 1
+        U = U - np.eye(nc)
     if nc == 2:
         comp = np.stack([U[..., 0, 0], U[..., 0, 1]], axis=1)   # [3][2][V]
     else:
