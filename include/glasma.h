@@ -78,7 +78,8 @@ typedef struct {
   int implicit_max_iter;    /* fixed-point iterations of the implicit scheme */
   double implicit_tol;      /* its convergence threshold on max |dE|; the
                                iteration also ends when max |dE| stops
-                               decreasing (the precision's rounding floor) */
+                               decreasing within 1024 unit roundoffs of
+                               max |E| (the precision's rounding floor) */
 } glasma_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both

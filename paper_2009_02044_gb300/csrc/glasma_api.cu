@@ -191,7 +191,7 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
     c->Uprev = ctx_alloc(c, ub);
     c->Uit = ctx_alloc(c, ub);
     c->Ework = ctx_alloc(c, eb);
-    c->conv = (double*)ctx_alloc(c, sizeof(double) * (p->implicit_max_iter + 1));
+    c->conv = (double*)ctx_alloc(c, sizeof(double) * 2 * (p->implicit_max_iter + 1));
   }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);

@@ -15,15 +15,28 @@
 // E(t_{n-1/2}) + dt J.  conv[k] is the largest |E^(k+1) - E^(k)| of
 // iteration k (atomicMax on the bit pattern of a non-negative double).
 // The iteration ends when that change is below implicit_tol or stops
-// decreasing (the rounding floor of the state's precision, reached first in
-// FP32); stopping above the floor would leave a same-signed truncation error
-// every step, which breaks the time symmetry of the scheme and makes the
-// energy drift.  Iteration k returns at once once either holds.
+// decreasing at the rounding floor of the state's precision (reached first in
+// FP32; see implicit_converged).  Iteration k returns at once once either
+// holds; if neither holds within implicit_max_iter the step reports
+// NOT_CONVERGED.
 #include <vector>
 
 #include "glasma_internal.cuh"
 
 namespace glasma {
+
+// Iteration k has converged if its largest change max|dE| is below the
+// tolerance, or if it no longer decreases while already within 1024 unit
+// roundoffs of max|E| (the rounding floor of the state's precision).  A
+// change that stops decreasing above that floor is a failing iteration
+// (e.g. dt^2 K_T / 4 > 1), not convergence.
+GL_HD bool implicit_converged(const double* conv, int maxit, int k, double tol, bool fp32) {
+  const double d = conv[k];
+  if (d < tol) return true;
+  if (k < 1 || d < conv[k - 1]) return false;
+  const double u = fp32 ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+  return d <= 1024.0 * u * conv[maxit + 1 + k];
+}
 
 template <typename R>
 struct ImplArgs {
@@ -37,7 +50,8 @@ struct ImplArgs {
   R* Ework;
   R* QA;
   R* QB;
-  double* conv;
+  double* conv;   // [k]: max |dE| of iteration k; [maxit + 1 + k]: max |E|
+  int maxit;
   int k;
   double tol;
   Geom g;
@@ -173,15 +187,12 @@ __global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  // converged earlier: below the tolerance, or no longer decreasing (the
-  // rounding floor of the state's precision)
-  if (a.k > 0 && a.conv[a.k - 1] < a.tol) return;
-  if (a.k > 1 && a.conv[a.k - 1] >= a.conv[a.k - 2]) return;
-  __shared__ double smax[6];
+  if (a.k > 0 && implicit_converged(a.conv, a.maxit, a.k - 1, a.tol, sizeof(R) == 4)) return;
+  __shared__ double smax[6], semax[6];
   const int i = (int)threadIdx.y;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const int iz = (int)blockIdx.y;
-  double dmax = 0.0;
+  double dmax = 0.0, emax = 0.0;
   const bool live = t < (uint32_t)a.g.nxy && !(i == 2 && iz == a.g.nz - 1);
   if (live) {
     const SiteNbr n = site_nbr_tz(a.g, t, iz);
@@ -195,6 +206,7 @@ __global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
       e[c] = a.Ework[idx] + a.dt * F[c];
       const double d = fabs((double)e[c] - (double)a.E[idx]);
       dmax = isfinite(d) ? fmax(dmax, d) : INFINITY;
+      emax = fmax(emax, fabs((double)e[c]));
       a.E[idx] = e[c];
     }
     M u = G::mul(G::expi(e, a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
@@ -203,14 +215,24 @@ __global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
   }
   // block max: warp shuffles, then one value per warp
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  }
   const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31, warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-  if (lane == 0) smax[warp] = dmax;
+  if (lane == 0) {
+    smax[warp] = dmax;
+    semax[warp] = emax;
+  }
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    double m = smax[0];
-    for (int w = 1; w < (int)(blockDim.x * blockDim.y) / 32; ++w) m = fmax(m, smax[w]);
+    double m = smax[0], me = semax[0];
+    for (int w = 1; w < (int)(blockDim.x * blockDim.y) / 32; ++w) {
+      m = fmax(m, smax[w]);
+      me = fmax(me, semax[w]);
+    }
     atomicMax((unsigned long long*)&a.conv[a.k], (unsigned long long)__double_as_longlong(m));
+    atomicMax((unsigned long long*)&a.conv[a.maxit + 1 + a.k], (unsigned long long)__double_as_longlong(me));
   }
 }
 
@@ -254,7 +276,8 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
     c->uprev_valid = true;
   }
   const int maxit = c->p.implicit_max_iter;
-  st = cuda_check(cudaMemsetAsync(c->conv, 0, sizeof(double) * (maxit + 1), c->stream), "conv clear");
+  a.maxit = maxit;
+  st = cuda_check(cudaMemsetAsync(c->conv, 0, sizeof(double) * 2 * (maxit + 1), c->stream), "conv clear");
   if (st) return st;
   a.Xn = (V2*)xa;
   k_implicit_prep<NC, R><<<grid, bs, 0, c->stream>>>(a);
@@ -268,8 +291,9 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
     st = cuda_check(cudaGetLastError(), "k_implicit_iter launch");
     if (st) return st;
   }
-  std::vector<double> conv(maxit);
-  st = cuda_check(cudaMemcpyAsync(conv.data(), c->conv, sizeof(double) * maxit, cudaMemcpyDeviceToHost, c->stream),
+  std::vector<double> conv(2 * (maxit + 1));
+  st = cuda_check(cudaMemcpyAsync(conv.data(), c->conv, sizeof(double) * conv.size(), cudaMemcpyDeviceToHost,
+                                  c->stream),
                   "conv readback");
   if (st) return st;
   st = cuda_check(cudaStreamSynchronize(c->stream), "implicit sync");
@@ -279,7 +303,7 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   for (int k = 0; k < maxit; ++k) {
     done = k + 1;
     if (!isfinite(conv[k])) return set_error(GLASMA_ERR_NONFINITE, "implicit iteration met a non-finite value");
-    if (conv[k] < a.tol || (k >= 1 && conv[k] >= conv[k - 1])) {
+    if (implicit_converged(conv.data(), maxit, k, a.tol, sizeof(R) == 4)) {
       converged = true;
       break;
     }

@@ -297,3 +297,45 @@ def test_implicit_not_converged_is_reported(G):
     assert e.value.code == "NOT_CONVERGED"
     # the step was still taken with the last iterate
     assert G.glasma_get_info(h).step_n == 1
+
+
+def test_implicit_failing_iteration_is_not_convergence(G):
+    """dt = a_T puts the fixed-point contraction dt^2 K_T / 4 near 2: the
+    iteration cannot settle, and the step must report NOT_CONVERGED instead
+    of accepting a stagnating iterate."""
+    cfg = gi.small_config(2, nz=48, nx=8, ny=8, a_z=1.0, dt=1.0, sigma_l=1.5,
+                          steps=4)
+    cfg.update(scheme="implicit", implicit_tol=1e-13, implicit_max_iter=40)
+    h = G.glasma_init_mv(cfg, None)
+    with pytest.raises(G.GlasmaError) as e:
+        G.glasma_step(h, 4)
+    assert e.value.code in ("NOT_CONVERGED", "NONFINITE")
+
+
+def _single_nucleus_energy(G, cfg, steps, every):
+    nt = cfg["nx"]
+    rho = gi.mv_rho(cfg["seed"], 2, nt, nt, cfg["g2mu"])
+    rho[0] = 0.0                                   # nucleus B alone
+    h = G.glasma_init_mv(cfg, rho)
+    H = [G.glasma_tmunu(h)[1]]
+    for _ in range(steps // every):
+        G.glasma_step(h, every)
+        H.append(G.glasma_tmunu(h)[1])
+    return np.array(H)
+
+
+def test_improved_scheme_is_stable_where_leapfrog_grows(G):
+    """A single thin nucleus (sigma_L = 2 a_T = 4 a_z) crossing the box at
+    a_z = 0.5 a_T: under the semi-implicit scheme at dt = a_z (dispersion
+    free along z, a hop every step) the field energy stays constant; under
+    leapfrog at the same a_z with dt = 0.375 (inside its Courant limit
+    0.408) numerical Cherenkov radiation makes it grow (FP64 both)."""
+    base = dict(nc=2, nz=640, nx=8, ny=8, a_t=1.0, a_z=0.5, sigma_l=2.0,
+                g2mu=0.05, m_ir=0.1, seed=77, z_offset=145.0, precision="fp64")
+    Hi = _single_nucleus_energy(G, dict(base, scheme="implicit", dt=0.5,
+                                        implicit_tol=1e-13, implicit_max_iter=80), 500, 50)
+    Hl = _single_nucleus_energy(G, dict(base, scheme="leapfrog", dt=0.375), 666, 66)
+    assert np.max(np.abs(Hi / Hi[0] - 1)) < 1e-4
+    # leapfrog: compare the same phase of its oscillation early and late
+    assert np.max(Hl[-3:]) > 1.05 * np.max(Hl[:3])
+    assert np.min(Hl[-3:]) > 1.05 * np.min(Hl[1:4])
