@@ -76,7 +76,8 @@ def bytes_per_site(nc, rs):
 def step_kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2009_02044_gb300", "csrc")
-    for f in ("k_step.cu", "lattice.cuh", "su_n.cuh"):
+    for f in ("k_step.cu", "step_link.cuh", "link_alg.cuh", "lattice.cuh",
+              "su_n.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -420,7 +421,61 @@ def run_extras(G, torch, cfg, args, stream, value):
             "max over z and sampled t (every 50 steps) of |eps32 - eps64| / "
             "max eps64; FP64 path parity-checked against the oracle"}
     out["improved"] = run_improved(G, torch, stream)
+    out["ensemble"] = run_ensemble(G, torch, stream)
     return out
+
+
+def run_ensemble(G, torch, stream, steps=40, warm=3):
+    """The 24-event ensemble (SU(3), 256 x {32^2, 48^2, 64^2}, FP32): the
+    events stepped one after another with glasma_step against one batched
+    launch per step (glasma_batch_step, block shape from glasma_batch_tune),
+    both from the same states, plus the ensemble mean of eps(z) after the
+    run (the event average of the energy density)."""
+    cfgs = gi.ensemble_configs()
+    sites = sum(c["nz"] * c["nx"] * c["ny"] for c in cfgs)
+    hs = []
+    with torch.cuda.stream(stream):
+        for c in cfgs:
+            hs.append(G.glasma_init_mv(c, None, stream=stream))
+    b = G.glasma_batch_create(hs)
+    G.glasma_batch_step(b, warm)
+    bx, persistent = G.glasma_batch_tune(b, 10)
+    blobs = [G.glasma_get_state(h) for h in hs]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for h in hs:
+        G.glasma_step(h, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = ev0.elapsed_time(ev1)
+    seq_tabs = [G.glasma_tmunu(h)[0] for h in hs]
+    for h, blob in zip(hs, blobs):
+        G.glasma_set_state(h, blob)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    G.glasma_batch_step(b, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_bat = ev0.elapsed_time(ev1)
+    tabs = [G.glasma_tmunu(h)[0] for h in hs]
+    same = all(np.array_equal(x, y) for x, y in zip(tabs, seq_tabs))
+    eps = np.array([t[:, 0] for t in tabs])
+    mean = eps.mean(axis=0)
+    zpk = int(np.argmax(mean))
+    b.close()
+    for h in hs:
+        G.glasma_free(h)
+    return {"workload": "su3_ensemble_24x256x{32,48,64}^2", "events": len(cfgs),
+            "value": sites * steps / (ms_bat * 1e-3), "unit": METRIC,
+            "sequential": sites * steps / (ms_seq * 1e-3),
+            "batched_over_sequential": ms_seq / ms_bat,
+            "block_sites": bx, "mode": "persistent" if persistent else "graph",
+            "steps_timed": steps,
+            "batched_equals_sequential": bool(same),
+            "eps_mean_peak": {"z": zpk, "value": float(mean[zpk]),
+                              "event_std": float(eps[:, zpk].std(ddof=1))}}
 
 
 def run_improved(G, torch, stream, steps=10, warm=3):

@@ -260,6 +260,60 @@ typedef struct {
 
 GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
 
+/*
+ * Batched ensemble (the event averages of Sec. 2 and Sec. 4): several
+ * independent leapfrog events, possibly of different nz, ny, nx, advanced
+ * together.  Each event's result is bitwise the one glasma_step gives it
+ * alone (the same per-link arithmetic).  Two execution modes:
+ *   graph (default): one kernel launch per time step over all events; the
+ *     launches of one call are captured on a private stream into one CUDA
+ *     graph, launched on the events' stream.  The call does not synchronise.
+ *   persistent: one cooperative launch per call, its blocks resident for
+ *     all the call's steps and meeting at a grid barrier between steps.
+ *     Every barrier wait is bounded (glasma_batch_set_barrier); a wait that
+ *     runs out makes the call return GLASMA_ERR_TIMEOUT, after which the
+ *     events' states are undefined (restore them from a checkpoint).  The
+ *     call synchronises the stream to read the barrier's status.
+ *
+ * glasma_batch_create: ctxs[0..n-1], 1 <= n <= 64, distinct contexts that
+ *   share nc, precision, dt, a_t, a_z, the device and the stream, all with
+ *   the leapfrog scheme.  The batch borrows the contexts (the caller keeps
+ *   ownership and must free the batch before any of them; 16 bytes of
+ *   barrier state come from the first context's allocator); *out receives
+ *   the handle.  Errors: INVALID_ARG, OOM, CUDA.
+ * glasma_batch_step: advance every event by n_steps steps.  Before a step in
+ *   which a charge of ANY event would leave its lattice, every event stops
+ *   after the last complete step and GLASMA_ERR_PARTICLE_EXIT is returned
+ *   (glasma_get_info gives each event's step_n).  Do not call it while the
+ *   stream is being captured.  Errors: INVALID_ARG, PARTICLE_EXIT, TIMEOUT
+ *   (persistent mode), CUDA.
+ * glasma_batch_set_shape: persistent 0 (graph) or 1, block_sites the
+ *   transverse sites per block (32, 64 or 128; a block is block_sites x 3
+ *   links).  Errors: INVALID_ARG.
+ * glasma_batch_tune: time `steps` batched steps in both modes with 32, 64
+ *   and 128 sites per block on the batch itself, keep the fastest for later
+ *   glasma_batch_step calls and store it in *block_sites and *persistent
+ *   (either may be NULL).  The events' states are saved before and restored
+ *   after each trial (temporary device copies of U, E and the charges,
+ *   through each context's allocator), so the call leaves every event as it
+ *   found it.  Synchronises the stream.  Without tuning: graph mode, 64.
+ *   Errors: INVALID_ARG, OOM, PARTICLE_EXIT (steps + 1 trial steps would
+ *   move a charge off a lattice), TIMEOUT, CUDA.
+ * glasma_batch_set_barrier: spin budget of one grid-barrier wait in SM clock
+ *   cycles (default 2e9, about a second) and extra_arrivals (0..1024, default
+ *   0), blocks that every barrier waits for in addition to the launched ones.
+ *   extra_arrivals > 0 makes every wait run out: it exists to test the
+ *   timeout path and has no other use.  Errors: INVALID_ARG.
+ * glasma_batch_free: release the batch (not the contexts).  NULL is ignored.
+ */
+typedef struct glasma_batch glasma_batch;
+GLASMA_API int glasma_batch_create(glasma_ctx* const* ctxs, int n, glasma_batch** out);
+GLASMA_API int glasma_batch_step(glasma_batch* b, int n_steps);
+GLASMA_API int glasma_batch_set_shape(glasma_batch* b, int persistent, int block_sites);
+GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, int* persistent);
+GLASMA_API int glasma_batch_set_barrier(glasma_batch* b, long long wait_cycles, int extra_arrivals);
+GLASMA_API void glasma_batch_free(glasma_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

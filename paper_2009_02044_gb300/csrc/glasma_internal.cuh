@@ -55,10 +55,10 @@ void* ctx_alloc(glasma_ctx* c, size_t bytes);
 void ctx_free(glasma_ctx* c, void* p);
 
 // number of hops after m steps: floor(m p/q + 1/2) in integers
-inline long long hop_count(long long m, long long p, long long q) {
+GL_HD long long hop_count(long long m, long long p, long long q) {
   return (2 * m * p + q) / (2 * q);
 }
-inline bool hop_at(long long n, long long p, long long q) {
+GL_HD bool hop_at(long long n, long long p, long long q) {
   return hop_count(n + 1, p, q) > hop_count(n, p, q);
 }
 

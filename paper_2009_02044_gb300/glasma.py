@@ -96,6 +96,14 @@ def load_library(path=LIB_PATH):
             C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                       C.c_double, C.c_double, P, P, P, C.c_int, C.c_int, P,
                       C.c_int, C.c_int, P, dp, dp, dp]),
+        "glasma_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int,
+                                          C.POINTER(C.c_void_p)]),
+        "glasma_batch_step": (C.c_int, [P, C.c_int]),
+        "glasma_batch_tune": (C.c_int, [P, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int)]),
+        "glasma_batch_set_shape": (C.c_int, [P, C.c_int, C.c_int]),
+        "glasma_batch_set_barrier": (C.c_int, [P, C.c_longlong, C.c_int]),
+        "glasma_batch_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -332,3 +340,64 @@ def glasma_gauss_residual_static(nc, precision, nz, ny, nx, a_t, a_z, U, E,
         C.c_void_p(QB), int(zB0), int(WB), C.c_void_p(s or 0),
         C.byref(m), C.byref(r), C.byref(q)), "glasma_gauss_residual_static")
     return m.value, r.value, q.value
+
+
+class Batch:
+    """Owns one glasma_batch* over borrowed contexts (kept alive here)."""
+
+    def __init__(self, ptr, handles):
+        self.ptr = ptr
+        self.handles = list(handles)
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            load_library().glasma_batch_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def glasma_batch_create(handles):
+    """One batch over Handles that share nc, precision, dt, a_t, a_z and
+    the stream (leapfrog scheme)."""
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    out = C.c_void_p()
+    _check(load_library().glasma_batch_create(arr, len(handles), C.byref(out)),
+           "glasma_batch_create")
+    return Batch(out, handles)
+
+
+def glasma_batch_step(b, n_steps):
+    _check(load_library().glasma_batch_step(b.ptr, int(n_steps)),
+           "glasma_batch_step")
+
+
+def glasma_batch_tune(b, steps=10):
+    """Time both modes with 32, 64 and 128 sites per block on the batch;
+    returns the kept (block_sites, persistent).  The events' states are
+    left as they were."""
+    bx, pers = C.c_int(), C.c_int()
+    _check(load_library().glasma_batch_tune(b.ptr, int(steps), C.byref(bx),
+                                            C.byref(pers)),
+           "glasma_batch_tune")
+    return bx.value, pers.value
+
+
+def glasma_batch_set_shape(b, persistent, block_sites):
+    _check(load_library().glasma_batch_set_shape(b.ptr, int(persistent),
+                                                 int(block_sites)),
+           "glasma_batch_set_shape")
+
+
+def glasma_batch_set_barrier(b, wait_cycles, extra_arrivals=0):
+    _check(load_library().glasma_batch_set_barrier(b.ptr, int(wait_cycles),
+                                                   int(extra_arrivals)),
+           "glasma_batch_set_barrier")
+
+
+def glasma_batch_free(b):
+    b.close()

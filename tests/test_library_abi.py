@@ -62,3 +62,20 @@ def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     with pytest.raises(G.GlasmaError) as e:
         G.glasma_init_mv(cfg, torch_memory=False)
     assert e.value.code == "INVALID_ARG"
+
+
+def test_batch_arguments_are_checked_on_the_host(lib):
+    import ctypes as C
+    from paper_2009_02044_gb300 import glasma as G
+    out = C.c_void_p()
+    assert lib.glasma_batch_create(None, 1, C.byref(out)) == -1
+    arr = (C.c_void_p * 1)(None)
+    assert lib.glasma_batch_create(arr, 0, C.byref(out)) == -1
+    assert lib.glasma_batch_create(arr, 65, C.byref(out)) == -1
+    assert lib.glasma_batch_create(arr, 1, C.byref(out)) == -1
+    assert out.value is None
+    assert lib.glasma_batch_step(None, 1) == -1
+    assert lib.glasma_batch_tune(None, 1, None, None) == -1
+    assert lib.glasma_batch_set_shape(None, 0, 64) == -1
+    assert lib.glasma_batch_set_barrier(None, 1000, 0) == -1
+    lib.glasma_batch_free(None)
