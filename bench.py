@@ -439,7 +439,7 @@ def run_ensemble(G, torch, stream, steps=40, warm=3):
             hs.append(G.glasma_init_mv(c, None, stream=stream))
     b = G.glasma_batch_create(hs)
     G.glasma_batch_step(b, warm)
-    bx, persistent = G.glasma_batch_tune(b, 10)
+    bx, mode = G.glasma_batch_tune(b, 10)
     blobs = [G.glasma_get_state(h) for h in hs]
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -471,7 +471,7 @@ def run_ensemble(G, torch, stream, steps=40, warm=3):
             "value": sites * steps / (ms_bat * 1e-3), "unit": METRIC,
             "sequential": sites * steps / (ms_seq * 1e-3),
             "batched_over_sequential": ms_seq / ms_bat,
-            "block_sites": bx, "mode": "persistent" if persistent else "graph",
+            "block_sites": bx, "mode": mode,
             "steps_timed": steps,
             "batched_equals_sequential": bool(same),
             "eps_mean_peak": {"z": zpk, "value": float(mean[zpk]),

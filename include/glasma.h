@@ -264,16 +264,21 @@ GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
  * Batched ensemble (the event averages of Sec. 2 and Sec. 4): several
  * independent leapfrog events, possibly of different nz, ny, nx, advanced
  * together.  Each event's result is bitwise the one glasma_step gives it
- * alone (the same per-link arithmetic).  Two execution modes:
- *   graph (default): one kernel launch per time step over all events; the
- *     launches of one call are captured on a private stream into one CUDA
- *     graph, launched on the events' stream.  The call does not synchronise.
- *   persistent: one cooperative launch per call, its blocks resident for
- *     all the call's steps and meeting at a grid barrier between steps.
- *     Every barrier wait is bounded (glasma_batch_set_barrier); a wait that
- *     runs out makes the call return GLASMA_ERR_TIMEOUT, after which the
- *     events' states are undefined (restore them from a checkpoint).  The
- *     call synchronises the stream to read the barrier's status.
+ * alone (the same per-link arithmetic).  Execution modes:
+ *   GLASMA_BATCH_GRAPH (default): one batched kernel launch per time step
+ *     over all events' work; the launches of one call are captured on a
+ *     private stream into one CUDA graph, launched on the events' stream.
+ *     The call does not synchronise.
+ *   GLASMA_BATCH_PERSISTENT: one cooperative launch per 64 steps, its
+ *     blocks resident throughout and meeting at a grid barrier between
+ *     steps.  Every barrier wait is bounded (glasma_batch_set_barrier); a
+ *     wait that runs out makes the call return GLASMA_ERR_TIMEOUT, after
+ *     which the events' states are undefined (restore them from a
+ *     checkpoint).  The call synchronises the stream to read the barrier's
+ *     status after each launch.
+ *   GLASMA_BATCH_PER_EVENT: the single-event step kernel of every event and
+ *     step captured into one graph (best for events that fill the GPU on
+ *     their own).  The call does not synchronise.
  *
  * glasma_batch_create: ctxs[0..n-1], 1 <= n <= 64, distinct contexts that
  *   share nc, precision, dt, a_t, a_z, the device and the stream, all with
@@ -285,18 +290,20 @@ GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
  *   which a charge of ANY event would leave its lattice, every event stops
  *   after the last complete step and GLASMA_ERR_PARTICLE_EXIT is returned
  *   (glasma_get_info gives each event's step_n).  Do not call it while the
- *   stream is being captured.  Errors: INVALID_ARG, PARTICLE_EXIT, TIMEOUT
+ *   stream is being captured, nor step the batch's contexts from another
+ *   thread meanwhile.  Errors: INVALID_ARG, PARTICLE_EXIT, TIMEOUT
  *   (persistent mode), CUDA.
- * glasma_batch_set_shape: persistent 0 (graph) or 1, block_sites the
- *   transverse sites per block (32, 64 or 128; a block is block_sites x 3
- *   links).  Errors: INVALID_ARG.
- * glasma_batch_tune: time `steps` batched steps in both modes with 32, 64
- *   and 128 sites per block on the batch itself, keep the fastest for later
- *   glasma_batch_step calls and store it in *block_sites and *persistent
- *   (either may be NULL).  The events' states are saved before and restored
- *   after each trial (temporary device copies of U, E and the charges,
- *   through each context's allocator), so the call leaves every event as it
- *   found it.  Synchronises the stream.  Without tuning: graph mode, 64.
+ * glasma_batch_set_shape: the mode and block_sites, the transverse sites
+ *   per block of the batched kernels (32, 64 or 128; a block is
+ *   block_sites x 3 links; ignored by the per-event mode).
+ *   Errors: INVALID_ARG.
+ * glasma_batch_tune: time `steps` steps in the graph and persistent modes
+ *   with 32, 64 and 128 sites per block and in the per-event mode, on the
+ *   batch itself; keep the fastest for later glasma_batch_step calls and
+ *   store it in *block_sites and *mode (either may be NULL).  The events'
+ *   states are saved before and restored after each trial (temporary device
+ *   copies of U, E and the charges, through each context's allocator), so
+ *   the call leaves every event as it found it.  Synchronises the stream.
  *   Errors: INVALID_ARG, OOM, PARTICLE_EXIT (steps + 1 trial steps would
  *   move a charge off a lattice), TIMEOUT, CUDA.
  * glasma_batch_set_barrier: spin budget of one grid-barrier wait in SM clock
@@ -306,11 +313,12 @@ GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
  *   timeout path and has no other use.  Errors: INVALID_ARG.
  * glasma_batch_free: release the batch (not the contexts).  NULL is ignored.
  */
+enum { GLASMA_BATCH_GRAPH = 0, GLASMA_BATCH_PERSISTENT = 1, GLASMA_BATCH_PER_EVENT = 2 };
 typedef struct glasma_batch glasma_batch;
 GLASMA_API int glasma_batch_create(glasma_ctx* const* ctxs, int n, glasma_batch** out);
 GLASMA_API int glasma_batch_step(glasma_batch* b, int n_steps);
-GLASMA_API int glasma_batch_set_shape(glasma_batch* b, int persistent, int block_sites);
-GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, int* persistent);
+GLASMA_API int glasma_batch_set_shape(glasma_batch* b, int mode, int block_sites);
+GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, int* mode);
 GLASMA_API int glasma_batch_set_barrier(glasma_batch* b, long long wait_cycles, int extra_arrivals);
 GLASMA_API void glasma_batch_free(glasma_batch* b);
 

@@ -21,6 +21,7 @@
 namespace glasma {
 
 constexpr int kMaxBatch = 64;  // kernel parameters: 64 x 112 B, under the 32 KB limit
+constexpr int kPersistSteps = 64;  // steps per persistent launch (one hop bit each)
 
 template <typename R>
 struct BatchEvent {
@@ -134,20 +135,20 @@ static int launch_batch(const BatchArgs<R>& b, uint32_t blocks, int bx, cudaStre
 
 template <typename R>
 struct PersistEvent {
-  typename V2T<R>::T* U[2];  // U[0]: links at the call's first step
+  typename V2T<R>::T* U[2];  // U[0]: links at the launch's first step
   R* E;
   R* QA;
   R* QB;
   Geom g;
-  int zA0, WA, zB0, WB;      // windows at the call's first step
-  long long n0, hp, hq;      // step index, hop ratio p/q
+  int zA0, WA, zB0, WB;      // windows at the launch's first step
+  unsigned long long hops;   // bit k: step k of the launch is a hop step
   uint32_t block0, ntb;
 };
 
 template <typename R>
 struct PersistArgs {
   int n;
-  int steps;
+  int steps;             // at most kPersistSteps
   R dt;
   R w[3];
   R az2;
@@ -200,7 +201,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned l
   return ok != 0;
 }
 
-template <int BX> struct PersistOcc { static constexpr int blocks = 576 / (3 * BX) > 0 ? 576 / (3 * BX) : 1; };
+template <int BX> struct PersistOcc { static constexpr int blocks = 480 / (3 * BX) > 0 ? 480 / (3 * BX) : 1; };
 
 template <int NC, typename R, int BX>
 __global__ void __launch_bounds__(3 * BX, sizeof(R) == 4 ? PersistOcc<BX>::blocks : 1)
@@ -215,9 +216,8 @@ __global__ void __launch_bounds__(3 * BX, sizeof(R) == 4 ? PersistOcc<BX>::block
       }
       const PersistEvent<R>& ev = a.ev[lo];
       const uint32_t local = w - ev.block0;
-      const long long h0 = hop_count(ev.n0, ev.hp, ev.hq);
-      const long long hk = hop_count(ev.n0 + k, ev.hp, ev.hq);
-      const int moved = (int)(hk - h0);
+      const unsigned long long below = ev.hops & ((1ull << k) - 1ull);
+      const int moved = __popcll(below);
       StepArgs<R> s;
       s.U = ev.U[k & 1];
       s.Un = ev.U[(k & 1) ^ 1];
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(3 * BX, sizeof(R) == 4 ? PersistOcc<BX>::block
       s.w[1] = a.w[1];
       s.w[2] = a.w[2];
       s.az2 = a.az2;
-      s.hop = hop_count(ev.n0 + k + 1, ev.hp, ev.hq) > hk ? 1 : 0;
+      s.hop = (int)((ev.hops >> k) & 1ull);
       s.zA0 = ev.zA0 - moved;
       s.WA = ev.WA;
       s.zB0 = ev.zB0 + moved;
@@ -276,7 +276,7 @@ static int launch_persistent(PersistArgs<R>& a, int bx, int extra_arrivals, cuda
 struct glasma_batch {
   std::vector<glasma_ctx*> ev;
   int bx = 64;                       // transverse sites per block
-  int persistent = 0;                // 0: graph of per-step launches, 1: one cooperative launch
+  int mode = GLASMA_BATCH_GRAPH;
   int device = 0;
   cudaStream_t stream = nullptr;     // the events' stream
   cudaStream_t capture = nullptr;    // private stream the graph is captured on
@@ -375,8 +375,7 @@ static int graph_run(glasma_batch* b, int steps, int bx) {
 // Persistent mode: one cooperative launch for all `steps` steps; reads the
 // barrier's error word back (synchronises the stream).
 template <int NC, typename R>
-static int persistent_run(glasma_batch* b, int steps, int bx) {
-  if (steps == 0) return GLASMA_OK;
+static int persistent_launch_run(glasma_batch* b, int steps, int bx) {
   const glasma_params& p = b->ev[0]->p;
   PersistArgs<R> a;
   a.n = (int)b->ev.size();
@@ -403,9 +402,9 @@ static int persistent_run(glasma_batch* b, int steps, int bx) {
     d.WA = c->WA;
     d.zB0 = c->zB0;
     d.WB = c->WB;
-    d.n0 = c->n;
-    d.hp = c->hop_p;
-    d.hq = c->hop_q;
+    d.hops = 0;
+    for (int k = 0; k < steps; ++k)
+      if (hop_at(c->n + k, c->hop_p, c->hop_q)) d.hops |= 1ull << k;
     d.block0 = block0;
     d.ntb = (uint32_t)((c->g.nxy + bx - 1) / bx);
     block0 += d.ntb * (uint32_t)c->g.nz;
@@ -427,20 +426,76 @@ static int persistent_run(glasma_batch* b, int steps, int bx) {
 }
 
 template <int NC, typename R>
-static int batch_run(glasma_batch* b, int n_steps, int persistent, int bx) {
+static int persistent_run(glasma_batch* b, int steps, int bx) {
+  int launches = 0;
+  for (int done = 0; done < steps; done += kPersistSteps) {
+    const int n = steps - done < kPersistSteps ? steps - done : kPersistSteps;
+    const int st = persistent_launch_run<NC, R>(b, n, bx);
+    if (st) return st;
+    ++launches;
+  }
+  for (glasma_ctx* c : b->ev) c->last_launches = launches;
+  b->last_launches = launches;
+  return GLASMA_OK;
+}
+
+// Per-event mode: the single-event step kernel of every event and step
+// captured into one graph (no batched kernel; for events that fill the GPU
+// on their own).  The contexts' streams and bookkeeping are pointed at the
+// capture while it runs and set back afterwards.
+static int per_event_run(glasma_batch* b, int steps) {
+  if (steps == 0) return GLASMA_OK;
+  const size_t ne = b->ev.size();
+  const EventCursor start(b);
+  EventCursor cs(b);
+  int st = cuda_check(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "batch capture begin");
+  if (st) return st;
+  for (int k = 0; k < steps && !st; ++k) {
+    for (size_t e = 0; e < ne && !st; ++e) {
+      glasma_ctx* c = b->ev[e];
+      c->stream = b->capture;
+      c->cur = cs.cur[e];
+      c->zA0 = cs.zA0[e];
+      c->zB0 = cs.zB0[e];
+      st = launch_step_leapfrog(c, hop_at(cs.n[e], c->hop_p, c->hop_q));
+      c->stream = b->stream;
+    }
+    cs.advance(b);
+  }
+  start.store(b, b->last_launches);
+  cudaGraph_t graph = nullptr;
+  const int st_end = cuda_check(cudaStreamEndCapture(b->capture, &graph), "batch capture end");
+  if (st || st_end) {
+    if (graph) cudaGraphDestroy(graph);
+    return st ? st : st_end;
+  }
+  cudaGraphExec_t exec = nullptr;
+  st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "batch graph instantiate");
+  if (!st) st = cuda_check(cudaGraphLaunch(exec, b->stream), "batch graph launch");
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (st) return st;
+  cs.store(b, steps * (int)ne);
+  return GLASMA_OK;
+}
+
+template <int NC, typename R>
+static int batch_run(glasma_batch* b, int n_steps, int mode, int bx) {
   const int allowed = steps_allowed(b, n_steps);
-  const int st = persistent ? persistent_run<NC, R>(b, allowed, bx) : graph_run<NC, R>(b, allowed, bx);
+  const int st = mode == GLASMA_BATCH_PERSISTENT ? persistent_run<NC, R>(b, allowed, bx)
+                 : mode == GLASMA_BATCH_PER_EVENT ? per_event_run(b, allowed)
+                                                  : graph_run<NC, R>(b, allowed, bx);
   if (st) return st;
   if (allowed < n_steps)
     return set_error(GLASMA_ERR_PARTICLE_EXIT, "a charge of a batched event would leave its lattice");
   return GLASMA_OK;
 }
 
-static int batch_dispatch(glasma_batch* b, int n_steps, int persistent, int bx) {
+static int batch_dispatch(glasma_batch* b, int n_steps, int mode, int bx) {
   const glasma_ctx* c = b->ev[0];
   if (c->p.nc == 2)
-    return c->rs == 8 ? batch_run<2, double>(b, n_steps, persistent, bx) : batch_run<2, float>(b, n_steps, persistent, bx);
-  return c->rs == 8 ? batch_run<3, double>(b, n_steps, persistent, bx) : batch_run<3, float>(b, n_steps, persistent, bx);
+    return c->rs == 8 ? batch_run<2, double>(b, n_steps, mode, bx) : batch_run<2, float>(b, n_steps, mode, bx);
+  return c->rs == 8 ? batch_run<3, double>(b, n_steps, mode, bx) : batch_run<3, float>(b, n_steps, mode, bx);
 }
 
 extern "C" {
@@ -482,13 +537,14 @@ GLASMA_API int glasma_batch_create(glasma_ctx* const* ctxs, int n, glasma_batch*
 GLASMA_API int glasma_batch_step(glasma_batch* b, int n_steps) {
   if (!b || n_steps < 0) return set_error(GLASMA_ERR_INVALID_ARG, "bad batch or n_steps");
   cudaSetDevice(b->device);
-  return batch_dispatch(b, n_steps, b->persistent, b->bx);
+  return batch_dispatch(b, n_steps, b->mode, b->bx);
 }
 
-GLASMA_API int glasma_batch_set_shape(glasma_batch* b, int persistent, int block_sites) {
-  if (!b || (persistent != 0 && persistent != 1) || (block_sites != 32 && block_sites != 64 && block_sites != 128))
-    return set_error(GLASMA_ERR_INVALID_ARG, "persistent must be 0 or 1 and block_sites 32, 64 or 128");
-  b->persistent = persistent;
+GLASMA_API int glasma_batch_set_shape(glasma_batch* b, int mode, int block_sites) {
+  if (!b || mode < GLASMA_BATCH_GRAPH || mode > GLASMA_BATCH_PER_EVENT ||
+      (block_sites != 32 && block_sites != 64 && block_sites != 128))
+    return set_error(GLASMA_ERR_INVALID_ARG, "unknown mode, or block_sites not 32, 64 or 128");
+  b->mode = mode;
   b->bx = block_sites;
   return GLASMA_OK;
 }
@@ -501,7 +557,7 @@ GLASMA_API int glasma_batch_set_barrier(glasma_batch* b, long long wait_cycles, 
   return GLASMA_OK;
 }
 
-GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, int* persistent) {
+GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, int* mode) {
   if (!b || steps < 1) return set_error(GLASMA_ERR_INVALID_ARG, "bad batch or steps");
   cudaSetDevice(b->device);
   if (steps_allowed(b, steps + 1) < steps + 1)
@@ -559,8 +615,9 @@ GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, i
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!st) st = cuda_check(cudaEventCreate(&e0), "event");
   if (!st) st = cuda_check(cudaEventCreate(&e1), "event");
-  for (int trial = 0; trial < 6 && !st; ++trial) {
-    const int mode = trial / 3, bx = shapes[trial % 3];
+  // batched graph and persistent with each block shape, then per-event
+  for (int trial = 0; trial < 7 && !st; ++trial) {
+    const int mode = trial == 6 ? GLASMA_BATCH_PER_EVENT : trial / 3, bx = trial == 6 ? 64 : shapes[trial % 3];
     st = batch_dispatch(b, 1, mode, bx);  // warm-up: module load, caches
     if (!st) st = cuda_check(cudaEventRecord(e0, b->stream), "event");
     if (!st) st = batch_dispatch(b, steps, mode, bx);
@@ -583,9 +640,9 @@ GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, i
     for (int k = 0; k < 4; ++k) ctx_free(b->ev[e], snap[e].buf[k]);
   if (st) return st;
   b->bx = best_bx;
-  b->persistent = best_mode;
+  b->mode = best_mode;
   if (block_sites) *block_sites = best_bx;
-  if (persistent) *persistent = best_mode;
+  if (mode) *mode = best_mode;
   return GLASMA_OK;
 }
 

@@ -376,19 +376,23 @@ def glasma_batch_step(b, n_steps):
            "glasma_batch_step")
 
 
+BATCH_MODES = {"graph": 0, "persistent": 1, "per_event": 2}
+
+
 def glasma_batch_tune(b, steps=10):
-    """Time both modes with 32, 64 and 128 sites per block on the batch;
-    returns the kept (block_sites, persistent).  The events' states are
-    left as they were."""
-    bx, pers = C.c_int(), C.c_int()
+    """Time every mode and block shape on the batch; returns the kept
+    (block_sites, mode name).  The events' states are left as they were."""
+    bx, mode = C.c_int(), C.c_int()
     _check(load_library().glasma_batch_tune(b.ptr, int(steps), C.byref(bx),
-                                            C.byref(pers)),
+                                            C.byref(mode)),
            "glasma_batch_tune")
-    return bx.value, pers.value
+    names = {v: k for k, v in BATCH_MODES.items()}
+    return bx.value, names[mode.value]
 
 
-def glasma_batch_set_shape(b, persistent, block_sites):
-    _check(load_library().glasma_batch_set_shape(b.ptr, int(persistent),
+def glasma_batch_set_shape(b, mode, block_sites=64):
+    """mode: "graph", "persistent" or "per_event"."""
+    _check(load_library().glasma_batch_set_shape(b.ptr, BATCH_MODES[mode],
                                                  int(block_sites)),
            "glasma_batch_set_shape")
 

@@ -1,7 +1,8 @@
 """GPU tests of the batched ensemble (glasma_batch_*): several independent
 events of uneven lattice size advanced by one kernel per step must give
 each event bitwise the state it gets alone from glasma_step (the same
-per-link arithmetic), and one batched event must match the FP64 oracle."""
+per-link arithmetic) in every execution mode, and one batched event must
+match the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -41,17 +42,18 @@ def _same(G, h1, h2):
     assert np.array_equal(G.glasma_tmunu(h1)[0], G.glasma_tmunu(h2)[0])
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("mode", ["graph", "persistent", "per_event"])
 @pytest.mark.parametrize("nc,precision", [(2, "fp64"), (3, "fp64"),
                                           (2, "fp32"), (3, "fp32")])
-def test_batch_is_bitwise_the_single_event_step(G, nc, precision, persistent):
+def test_batch_is_bitwise_the_single_event_step(G, nc, precision, mode):
     cfgs = _cfgs(nc, precision)
     single = [G.glasma_init_mv(c, None) for c in cfgs]
     batched = [G.glasma_init_mv(c, None) for c in cfgs]
     b = G.glasma_batch_create(batched)
-    G.glasma_batch_set_shape(b, persistent, 64)
+    G.glasma_batch_set_shape(b, mode, 64)
     G.glasma_batch_step(b, 7)      # two calls: bookkeeping carried over
     G.glasma_batch_step(b, 13)
+    G.glasma_batch_step(b, 0)
     for h in single:
         G.glasma_step(h, 20)
     for h1, h2 in zip(single, batched):
@@ -60,14 +62,14 @@ def test_batch_is_bitwise_the_single_event_step(G, nc, precision, persistent):
     b.close()
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("mode", ["graph", "persistent"])
 @pytest.mark.parametrize("block_sites", [32, 128])
-def test_every_block_shape_is_bitwise(G, persistent, block_sites):
+def test_every_block_shape_is_bitwise(G, mode, block_sites):
     cfgs = _cfgs(3, "fp32")
     single = [G.glasma_init_mv(c, None) for c in cfgs]
     batched = [G.glasma_init_mv(c, None) for c in cfgs]
     b = G.glasma_batch_create(batched)
-    G.glasma_batch_set_shape(b, persistent, block_sites)
+    G.glasma_batch_set_shape(b, mode, block_sites)
     G.glasma_batch_step(b, 11)
     for h in single:
         G.glasma_step(h, 11)
@@ -98,8 +100,8 @@ def test_tune_keeps_the_state_and_the_result(G, precision):
     for h in single + batched:
         G.glasma_step(h, 3)
     b = G.glasma_batch_create(batched)
-    bx, persistent = G.glasma_batch_tune(b, 4)
-    assert bx in (32, 64, 128) and persistent in (0, 1)
+    bx, mode = G.glasma_batch_tune(b, 4)
+    assert bx in (32, 64, 128) and mode in G.BATCH_MODES
     for h1, h2 in zip(single, batched):
         _same(G, h1, h2)            # tuning left every event as it was
     G.glasma_batch_step(b, 9)
@@ -109,8 +111,8 @@ def test_tune_keeps_the_state_and_the_result(G, precision):
         _same(G, h1, h2)
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
-def test_particle_exit_stops_every_event_at_the_same_step(G, persistent):
+@pytest.mark.parametrize("mode", ["graph", "persistent", "per_event"])
+def test_particle_exit_stops_every_event_at_the_same_step(G, mode):
     short = gi.small_config(2, nz=48, steps=0, seed=5)
     long_ = gi.small_config(2, nz=96, nx=6, ny=7, steps=0, seed=6)
     probe = G.glasma_init_mv(short, None)
@@ -119,7 +121,7 @@ def test_particle_exit_stops_every_event_at_the_same_step(G, persistent):
     n_exit = G.glasma_get_info(probe).step_n
     hs = [G.glasma_init_mv(c, None) for c in (short, long_)]
     b = G.glasma_batch_create(hs)
-    G.glasma_batch_set_shape(b, persistent, 64)
+    G.glasma_batch_set_shape(b, mode, 64)
     with pytest.raises(G.GlasmaError) as e:
         G.glasma_batch_step(b, 400)
     assert e.value.code == "PARTICLE_EXIT"
@@ -151,7 +153,7 @@ def test_barrier_wait_that_runs_out_returns_timeout(G):
     hs = [G.glasma_init_mv(c, None) for c in cfgs]
     blobs = [G.glasma_get_state(h) for h in hs]
     b = G.glasma_batch_create(hs)
-    G.glasma_batch_set_shape(b, 1, 64)
+    G.glasma_batch_set_shape(b, "persistent", 64)
     G.glasma_batch_set_barrier(b, 1_000_000, extra_arrivals=1)
     G.glasma_batch_step(b, 1)          # one step has no barrier
     with pytest.raises(G.GlasmaError) as e:
@@ -165,4 +167,22 @@ def test_barrier_wait_that_runs_out_returns_timeout(G):
     ref = [G.glasma_init_mv(c, None) for c in cfgs]
     for h1, h2 in zip(ref, hs):
         G.glasma_step(h1, 5)
+        _same(G, h1, h2)
+
+
+def test_persistent_call_longer_than_one_launch(G):
+    """150 steps: three cooperative launches of at most 64 steps, the hop
+    schedule and the windows carried from one launch to the next."""
+    cfgs = [dict(gi.small_config(2, nz=nz, nx=nx, ny=ny, seed=40 + k),
+                 precision="fp32")
+            for k, (nz, nx, ny) in enumerate([(200, 9, 8), (208, 16, 4)])]
+    single = [G.glasma_init_mv(c, None) for c in cfgs]
+    batched = [G.glasma_init_mv(c, None) for c in cfgs]
+    b = G.glasma_batch_create(batched)
+    G.glasma_batch_set_shape(b, "persistent", 64)
+    G.glasma_batch_step(b, 150)
+    assert G.glasma_get_info(batched[0]).kernel_launches == 3
+    for h in single:
+        G.glasma_step(h, 150)
+    for h1, h2 in zip(single, batched):
         _same(G, h1, h2)
