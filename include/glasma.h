@@ -163,6 +163,15 @@ GLASMA_API int glasma_gauss_residual(glasma_ctx* c, double* max_abs, double* rms
 GLASMA_API int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total);
 
 /*
+ * The same table as glasma_tmunu, written to device memory on the context's
+ * stream without synchronising, for sampling T^{mu nu}(t, z) during a run.
+ * dev_out: device doubles [nz][4] (eps, p_L, p_T, S_L), 8-byte aligned,
+ * owned by the caller.  A slice whose sums met a non-finite value gets a
+ * NaN eps (no status: nothing is read back).  Errors: INVALID_ARG, CUDA.
+ */
+GLASMA_API int glasma_tmunu_device(glasma_ctx* c, double* dev_out);
+
+/*
  * Gauss-law residual of fields the caller owns, computed without allocating
  * any device memory.  The paper has no counterpart of this call: it exists
  * for callers that cannot call cudaMalloc -- for example a health check that
@@ -259,6 +268,42 @@ typedef struct {
 } glasma_info;
 
 GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
+
+/*
+ * Rest-frame analysis of sampled tables (Sec. 4: the event average of
+ * T^{mu nu}, its diagonalisation to the local rest-frame energy density
+ * eps_loc, Milne coordinates tau = sqrt(t^2 - z^2), eta_s, and the Gaussian
+ * fit of rapidity profiles, Fig. 4).  Device arrays are FP64 and owned by
+ * the caller; work runs on `stream` (cudaStream_t, NULL = legacy default)
+ * without synchronising.
+ *
+ * glasma_rest_frame: tabs [n_events][n_points][4] rows (eps, p_L, p_T, S_L)
+ *   as glasma_tmunu_device writes them (n_points = samples x nz, 32-byte
+ *   aligned); out [n_points][8] = (<eps>, <p_L>, <p_T>, <S_L>, eps_loc,
+ *   p_L,loc, v_z, valid) with <.> the mean over events (summed in event
+ *   order).  eps_loc and -p_L,loc are the eigenvalues of T^mu_nu on the
+ *   (t, z) block (metric diag(+1, -1)) whose eigenvectors are timelike and
+ *   spacelike, v_z = u^z / u^t the flow velocity.  A point with S_L != 0
+ *   and (eps + p_L)^2 <= 4 S_L^2 has no timelike eigenvector: its eps_loc,
+ *   p_L,loc, v_z are NaN and valid is 0 (1 otherwise).
+ *   Errors: INVALID_ARG, CUDA.
+ * glasma_sample_grid: component comp of grid [n_t][nz][stride] (point
+ *   (k, j) at t = t0 + k dts, z = z0 + j az), interpolated bilinearly at
+ *   n_pts points given as (tau, eta_s) (coords 0; t = tau cosh eta_s,
+ *   z = tau sinh eta_s, eta_s = artanh(z / t)) or as (t, z) (coords 1) in
+ *   x[i], y[i]; out[i] is NaN outside the grid.  Errors: INVALID_ARG, CUDA.
+ * glasma_fit_gaussian (host arrays, host computation): fits
+ *   f = amp exp(-(x - mu)^2 / (2 sigma^2)) by weighted least squares of
+ *   log f on a parabola (weights f^2) over the finite points with
+ *   f > frac * max f.  Errors: INVALID_ARG (fewer than 3 points, no
+ *   maximum).
+ */
+GLASMA_API int glasma_rest_frame(const double* tabs, int n_events, long long n_points, double* out, void* stream);
+GLASMA_API int glasma_sample_grid(const double* grid, int n_t, int nz, int stride, int comp, double t0,
+                                  double dts, double z0, double az, const double* x, const double* y,
+                                  long long n_pts, int coords, double* out, void* stream);
+GLASMA_API int glasma_fit_gaussian(const double* x, const double* f, int n, double frac, double* amp, double* mu,
+                                   double* sigma);
 
 /*
  * Batched ensemble (the event averages of Sec. 2 and Sec. 4): several

@@ -286,6 +286,13 @@ int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total) {
   return GLASMA_OK;
 }
 
+int glasma_tmunu_device(glasma_ctx* c, double* dev_out) {
+  if (!c || !dev_out) return set_error(GLASMA_ERR_INVALID_ARG, "context or dev_out is NULL");
+  if (((uintptr_t)dev_out & 7) != 0) return set_error(GLASMA_ERR_INVALID_ARG, "dev_out must be 8-byte aligned");
+  cudaSetDevice(c->device);
+  return launch_tmunu(c, hop_at(c->n, c->hop_p, c->hop_q), nullptr, dev_out);
+}
+
 // ---------------------------------------------------------------------------
 // fields in FP64 (host marshalling of the device layout)
 // ---------------------------------------------------------------------------

@@ -66,7 +66,9 @@ GL_HD bool hop_at(long long n, long long p, long long q) {
 int launch_step_leapfrog(glasma_ctx* c, bool hop);
 int launch_step_implicit(glasma_ctx* c, bool hop, int* iters);
 int launch_gauss(glasma_ctx* c, double* out3);
-int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab);
+// host_tab != NULL: read the table back and synchronise; dev_tab != NULL:
+// write the table there instead of the context's own buffer
+int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab = nullptr);
 int run_init(glasma_ctx* c, const double* rho_host);
 
 // checkpoint CRC-32 (IEEE 802.3 polynomial, reflected)

@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
 }
 
 template <int NC, typename R>
-static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab) {
+static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab) {
   TmnArgs<R> a;
   a.U = (const typename V2T<R>::T*)c->U[c->cur];
   a.E = (const R*)c->E;
@@ -320,10 +320,10 @@ static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
-  a.tab = c->tab;
+  a.tab = dev_tab ? dev_tab : c->tab;
   k_tmunu<NC, R><<<c->g.nz, kRedThreads, 0, c->stream>>>(a);
   int st = cuda_check(cudaGetLastError(), "k_tmunu launch");
-  if (st) return st;
+  if (st || !host_tab) return st;
   st = cuda_check(cudaMemcpyAsync(host_tab, c->tab, sizeof(double) * 4 * c->g.nz, cudaMemcpyDeviceToHost,
                                   c->stream),
                   "tmunu readback");
@@ -331,9 +331,10 @@ static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab) {
   return cuda_check(cudaStreamSynchronize(c->stream), "tmunu sync");
 }
 
-int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab) {
-  if (c->p.nc == 2) return c->rs == 8 ? tmunu_t<2, double>(c, hop, host_tab) : tmunu_t<2, float>(c, hop, host_tab);
-  return c->rs == 8 ? tmunu_t<3, double>(c, hop, host_tab) : tmunu_t<3, float>(c, hop, host_tab);
+int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab) {
+  if (c->p.nc == 2)
+    return c->rs == 8 ? tmunu_t<2, double>(c, hop, host_tab, dev_tab) : tmunu_t<2, float>(c, hop, host_tab, dev_tab);
+  return c->rs == 8 ? tmunu_t<3, double>(c, hop, host_tab, dev_tab) : tmunu_t<3, float>(c, hop, host_tab, dev_tab);
 }
 
 }  // namespace glasma

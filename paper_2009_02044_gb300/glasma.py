@@ -96,6 +96,14 @@ def load_library(path=LIB_PATH):
             C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                       C.c_double, C.c_double, P, P, P, C.c_int, C.c_int, P,
                       C.c_int, C.c_int, P, dp, dp, dp]),
+        "glasma_tmunu_device": (C.c_int, [P, P]),
+        "glasma_rest_frame": (C.c_int, [P, C.c_int, C.c_longlong, P, P]),
+        "glasma_sample_grid": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                         C.c_double, C.c_double, C.c_double,
+                                         C.c_double, P, P, C.c_longlong,
+                                         C.c_int, P, P]),
+        "glasma_fit_gaussian": (C.c_int, [dp, dp, C.c_int, C.c_double, dp, dp,
+                                          dp]),
         "glasma_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int,
                                           C.POINTER(C.c_void_p)]),
         "glasma_batch_step": (C.c_int, [P, C.c_int]),
@@ -405,3 +413,47 @@ def glasma_batch_set_barrier(b, wait_cycles, extra_arrivals=0):
 
 def glasma_batch_free(b):
     b.close()
+
+
+def _stream_ptr(stream):
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    return C.c_void_p(s or 0)
+
+
+def glasma_tmunu_device(h, dev_out):
+    """T^{mu nu} table [nz][4] into device memory at address dev_out (an
+    int, e.g. tensor.data_ptr()), on the context's stream, no sync."""
+    _check(load_library().glasma_tmunu_device(h.ptr, C.c_void_p(dev_out)),
+           "glasma_tmunu_device")
+
+
+def glasma_rest_frame(tabs, n_events, n_points, out, stream=None):
+    """Event mean and local rest frame (device addresses; see
+    include/glasma.h): tabs [n_events][n_points][4] -> out
+    [n_points][8]."""
+    _check(load_library().glasma_rest_frame(
+        C.c_void_p(tabs), int(n_events), int(n_points), C.c_void_p(out),
+        _stream_ptr(stream)), "glasma_rest_frame")
+
+
+def glasma_sample_grid(grid, n_t, nz, stride, comp, t0, dts, z0, az, x, y,
+                       n_pts, out, coords="milne", stream=None):
+    """Bilinear samples of grid [n_t][nz][stride] component comp at
+    (tau, eta_s) (coords "milne") or (t, z) (coords "lab") points; device
+    addresses."""
+    _check(load_library().glasma_sample_grid(
+        C.c_void_p(grid), int(n_t), int(nz), int(stride), int(comp),
+        float(t0), float(dts), float(z0), float(az), C.c_void_p(x),
+        C.c_void_p(y), int(n_pts), {"milne": 0, "lab": 1}[coords],
+        C.c_void_p(out), _stream_ptr(stream)), "glasma_sample_grid")
+
+
+def glasma_fit_gaussian(x, f, frac=0.1):
+    """(amp, mu, sigma) of the Gaussian fitted to host arrays x, f."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    amp, mu, sig = C.c_double(), C.c_double(), C.c_double()
+    _check(load_library().glasma_fit_gaussian(
+        _dptr(x), _dptr(f), len(x), float(frac), C.byref(amp), C.byref(mu),
+        C.byref(sig)), "glasma_fit_gaussian")
+    return amp.value, mu.value, sig.value

@@ -4,6 +4,7 @@ touching the GPU."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 import glasma_inputs as gi
@@ -79,3 +80,25 @@ def test_batch_arguments_are_checked_on_the_host(lib):
     assert lib.glasma_batch_set_shape(None, 0, 64) == -1
     assert lib.glasma_batch_set_barrier(None, 1000, 0) == -1
     lib.glasma_batch_free(None)
+
+
+def test_host_gaussian_fit_matches_oracle(lib):
+    """glasma_fit_gaussian is host code: checked here against the oracle's
+    numpy.polyfit fit on exact and on noisy profiles."""
+    from oracle import rest_frame as RF
+    from paper_2009_02044_gb300 import glasma as G
+    eta = np.linspace(-3, 3, 97)
+    f = 1.25 * np.exp(-(eta + 0.4) ** 2 / (2 * 0.8 ** 2))
+    a, m, s = G.glasma_fit_gaussian(eta, f, 0.02)
+    assert abs(a - 1.25) < 1e-11 and abs(m + 0.4) < 1e-11 and abs(s - 0.8) < 1e-11
+    rng = np.random.default_rng(5)
+    for k in range(20):
+        fn = f * (1 + 0.05 * rng.standard_normal(eta.size)) + 0.01 * rng.random()
+        frac = (0.05, 0.2, 0.5)[k % 3]
+        got = np.array(G.glasma_fit_gaussian(eta, fn, frac))
+        ref = np.array(RF.fit_gaussian(eta, fn, frac))
+        assert np.allclose(got, ref, rtol=1e-10, atol=0), (got, ref)
+    with pytest.raises(G.GlasmaError):
+        G.glasma_fit_gaussian(eta, np.exp(eta ** 2 / 8), 0.0)
+    with pytest.raises(G.GlasmaError):
+        G.glasma_fit_gaussian(eta[:2], f[:2], 0.0)
