@@ -489,6 +489,8 @@ def run_observables(G, torch, stream, every=4, steps=200):
     except G.GlasmaError as ex:
         res["sigma_eta_tau50"] = None
         res["fit"] = str(ex)
+    res["eps_loc_tau50_every4"] = [float("%.4g" % v) for v in last[::4]]
+    res["eta_every4"] = [float("%.3g" % v) for v in eta_h[::4]]
     mid = len(eta_h) // 2
     te = [tau * float(prof[tau][0][mid].item()) for tau in taus]
     res["tau_eps_loc_eta0"] = dict(zip([str(t) for t in taus], te))
