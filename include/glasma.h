@@ -306,6 +306,26 @@ GLASMA_API int glasma_fit_gaussian(const double* x, const double* f, int n, doub
                                    double* sigma);
 
 /*
+ * Gradient of the mid-rapidity energy with respect to the initial MV colour
+ * charges (SU(2), FP64, leapfrog): the hand-written adjoint of
+ * glasma_init_mv followed by n_steps glasma_step calls.  The observable is
+ *   O = a_z sum_{iz : |iz a_z - z_c| < half_width} eps(iz)
+ * with eps(iz) the energy density of glasma_tmunu at step n_steps (Sec. 4)
+ * and z_c = nz a_z / 2.  rho_host: [2][3][ny][nx] charges as for
+ * glasma_init_mv (NULL: drawn from p->seed).  The forward run keeps a
+ * state every checkpoint_every steps; the reverse pass recomputes each
+ * segment from its checkpoint (device memory: (ceil(n_steps / K) +
+ * min(K, n_steps) + 2) states plus about 70 doubles per site, through
+ * `alloc` as in glasma_init_mv).  Outputs: *value = O (may be NULL) and
+ * grad_host[2][3][ny][nx] = dO/drho (NULL: forward only).  Synchronises
+ * the stream.  Errors: INVALID_ARG (not SU(2)/FP64/leapfrog, bad sizes),
+ * PARTICLE_EXIT, OOM, CUDA.
+ */
+GLASMA_API int glasma_adjoint_energy(const glasma_params* p, const double* rho_host, int n_steps,
+                                     double half_width, int checkpoint_every, void* stream,
+                                     const glasma_allocator* alloc, double* value, double* grad_host);
+
+/*
  * Batched ensemble (the event averages of Sec. 2 and Sec. 4): several
  * independent leapfrog events, possibly of different nz, ny, nx, advanced
  * together.  Each event's result is bitwise the one glasma_step gives it

@@ -70,6 +70,10 @@ int launch_gauss(glasma_ctx* c, double* out3);
 // write the table there instead of the context's own buffer
 int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab = nullptr);
 int run_init(glasma_ctx* c, const double* rho_host);
+int device_philox_rho(const glasma_params& p, int na, double* rho, cudaStream_t s);
+int device_poisson(const glasma_params& p, const double* in, double* out, int F, double2* w0, double2* w1,
+                   cudaStream_t s);
+int device_profile(const glasma_params& p, double* lam, cudaStream_t s);
 
 // checkpoint CRC-32 (IEEE 802.3 polynomial, reflected)
 uint32_t crc32(const void* data, size_t n, uint32_t crc = 0);

@@ -337,6 +337,36 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
   return st;
 }
 
+// Device helpers shared with the adjoint: the MV draw, the transverse
+// Poisson solve of F real [ny][nx] fields (in and out may alias; w0, w1 hold
+// F*nx*ny complex values each) and the profile table lam[(t*2 + N)*nz + iz].
+int device_philox_rho(const glasma_params& p, int na, double* rho, cudaStream_t s) {
+  const int64_t n = (int64_t)2 * na * p.nx * p.ny;
+  k_philox_rho<<<grid_for(n), 256, 0, s>>>(rho, na, p.nx, p.ny, p.seed, p.g2mu);
+  return cuda_check(cudaGetLastError(), "philox rho");
+}
+
+int device_poisson(const glasma_params& p, const double* in, double* out, int F, double2* w0, double2* w1,
+                   cudaStream_t s) {
+  const int64_t nxy = (int64_t)p.nx * p.ny, n = F * nxy;
+  k_real_to_cplx<<<grid_for(n), 256, 0, s>>>(in, w0, n);
+  k_dft<<<grid_for(n), 256, 0, s>>>(w0, w1, F, p.ny, p.nx, 0, -1);
+  k_dft<<<grid_for(n), 256, 0, s>>>(w1, w0, F, p.ny, p.nx, 1, -1);
+  k_poisson_kernel<<<grid_for(n), 256, 0, s>>>(w0, F, p.ny, p.nx, p.a_t, p.m_ir * p.m_ir,
+                                                p.uv_cutoff > 0 ? p.uv_cutoff * p.uv_cutoff : 0.0);
+  k_dft<<<grid_for(n), 256, 0, s>>>(w0, w1, F, p.ny, p.nx, 1, +1);
+  k_dft<<<grid_for(n), 256, 0, s>>>(w1, w0, F, p.ny, p.nx, 0, +1);
+  k_cplx_real_scaled<<<grid_for(n), 256, 0, s>>>(w0, out, n, 1.0 / (double)nxy);
+  return cuda_check(cudaGetLastError(), "poisson");
+}
+
+int device_profile(const glasma_params& p, double* lam, cudaStream_t s) {
+  const double zc = p.nz * p.a_z / 2.0;
+  const double d = p.z_offset > 0 ? p.z_offset : (ceil(4.0 * p.sigma_l / p.a_z) + 2.0) * p.a_z;
+  k_profile<<<grid_for(4 * p.nz), 256, 0, s>>>(lam, p.nz, p.a_z, p.sigma_l, zc + d, zc - d, p.dt);
+  return cuda_check(cudaGetLastError(), "profile");
+}
+
 int run_init(glasma_ctx* c, const double* rho_host) {
   if (c->p.nc == 2) return c->rs == 8 ? init_t<2, double>(c, rho_host) : init_t<2, float>(c, rho_host);
   return c->rs == 8 ? init_t<3, double>(c, rho_host) : init_t<3, float>(c, rho_host);

@@ -104,6 +104,10 @@ def load_library(path=LIB_PATH):
                                          C.c_int, P, P]),
         "glasma_fit_gaussian": (C.c_int, [dp, dp, C.c_int, C.c_double, dp, dp,
                                           dp]),
+        "glasma_adjoint_energy": (C.c_int, [C.POINTER(glasma_params), dp,
+                                            C.c_int, C.c_double, C.c_int, P,
+                                            C.POINTER(glasma_allocator), dp,
+                                            dp]),
         "glasma_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int,
                                           C.POINTER(C.c_void_p)]),
         "glasma_batch_step": (C.c_int, [P, C.c_int]),
@@ -457,3 +461,60 @@ def glasma_fit_gaussian(x, f, frac=0.1):
         _dptr(x), _dptr(f), len(x), float(frac), C.byref(amp), C.byref(mu),
         C.byref(sig)), "glasma_fit_gaussian")
     return amp.value, mu.value, sig.value
+
+
+def glasma_adjoint_energy(cfg, rho, n_steps, half_width, checkpoint_every=20,
+                          stream=None, grad=True, torch_memory=True):
+    """O = a_z sum_{|z - z_c| < half_width} eps(z) after n_steps from the
+    MV charges rho [2][3][ny][nx] (SU(2), FP64, leapfrog) and, if grad,
+    dO/drho from the hand-written adjoint (include/glasma.h).
+    Returns (O, gradient array or None)."""
+    lib = load_library()
+    p = make_params(cfg)
+    r = None
+    if rho is not None:
+        r = np.ascontiguousarray(rho, dtype=np.float64)
+        if r.shape != (2, 3, p.ny, p.nx):
+            raise ValueError("rho must have shape (2, 3, %d, %d)" % (p.ny, p.nx))
+    keep = None
+    alloc_ptr = None
+    if torch_memory:
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        a, keep = _torch_allocator()
+        alloc_ptr = C.byref(a)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    val = C.c_double()
+    g = np.zeros((2, 3, p.ny, p.nx)) if grad else None
+    st = lib.glasma_adjoint_energy(C.byref(p), _dptr(r), int(n_steps),
+                                   float(half_width), int(checkpoint_every),
+                                   C.c_void_p(s or 0), alloc_ptr,
+                                   C.byref(val), _dptr(g))
+    del keep
+    _check(st, "glasma_adjoint_energy")
+    return val.value, g
+
+
+def mid_rapidity_energy(rho, cfg, n_steps, half_width, checkpoint_every=20):
+    """The observable as a differentiable torch function of rho (float64
+    tensor [2][3][ny][nx] on any device): forward runs the simulation, the
+    backward pass calls the CUDA adjoint."""
+    import torch
+
+    class _MidEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, r):
+            host = r.detach().to("cpu", torch.float64).numpy()
+            val, _ = glasma_adjoint_energy(cfg, host, n_steps, half_width,
+                                           checkpoint_every, grad=False)
+            ctx.host = host
+            return r.new_tensor(val)
+
+        @staticmethod
+        def backward(ctx, go):
+            _, g = glasma_adjoint_energy(cfg, ctx.host, n_steps, half_width,
+                                         checkpoint_every, grad=True)
+            return go * torch.from_numpy(g).to(go.device, go.dtype)
+
+    return _MidEnergy.apply(rho)
