@@ -27,7 +27,7 @@ def G():
 
 SMALL = [
     (gi.small_config(2, nz=40, nx=5, ny=4, seed=3), 24, 8.0),
-    (gi.small_config(2, nz=48, nx=4, ny=6, seed=9, a_z=0.5, dt=0.25), 30, 5.0),
+    (gi.small_config(2, nz=96, nx=4, ny=6, seed=9, a_z=0.5, dt=0.25), 30, 5.0),
     (gi.small_config(2, nz=56, nx=12, ny=10, seed=4), 33, 12.0),
     (gi.small_config(2, nz=40, nx=5, ny=4, seed=3), 0, 8.0),
 ]
