@@ -129,15 +129,25 @@ def _u53(hi, lo):
     return (a * 67108864.0 + b + 0.5) * (1.0 / 9007199254740992.0)
 
 
-def mv_rho(seed, nc, nx, ny, g2mu):
-    """MV colour charges rho[N][a][y][x] (N = 0: nucleus A, 1: nucleus B).
+def mv_rho(seed, nc, nx, ny, g2mu, sheets=1):
+    """MV colour charges rho[N][a][y][x] (N = 0: nucleus A, 1: nucleus B);
+    with sheets = S > 1, rho[s][N][a][y][x] for S independent longitudinal
+    colour sheets, each with standard deviation g2mu / sqrt(S) so that the
+    charge summed over the sheets keeps the single-sheet variance.
 
-    Counter = (x, y, a, N), key = (seed low word, seed high word); the four
-    output words give two 53-bit uniforms u1, u2 and one Box-Muller normal
-    sqrt(-2 ln u1) cos(2 pi u2), scaled by g2mu."""
+    Counter = (x, y, a, N + 2 s), key = (seed low word, seed high word); the
+    four output words give two 53-bit uniforms u1, u2 and one Box-Muller
+    normal sqrt(-2 ln u1) cos(2 pi u2), scaled by the standard deviation."""
     na = nc * nc - 1
-    N, A, Y, X = np.meshgrid(np.arange(2), np.arange(na), np.arange(ny),
-                             np.arange(nx), indexing="ij")
+    if sheets > 1:
+        S, N, A, Y, X = np.meshgrid(np.arange(sheets), np.arange(2),
+                                    np.arange(na), np.arange(ny),
+                                    np.arange(nx), indexing="ij")
+        N = N + 2 * S
+        g2mu = g2mu / np.sqrt(sheets)
+    else:
+        N, A, Y, X = np.meshgrid(np.arange(2), np.arange(na), np.arange(ny),
+                                 np.arange(nx), indexing="ij")
     seed = int(seed)
     k0 = np.uint32(seed & 0xFFFFFFFF)
     k1 = np.uint32((seed >> 32) & 0xFFFFFFFF)

@@ -196,6 +196,7 @@ class Params:
     uv_cutoff: float = 0.0
     z_offset: float = 0.0
     seed: int = 0
+    n_sheets: int = 1
 
     @staticmethod
     def from_dict(d):
@@ -310,6 +311,34 @@ def wilson_line_dag(phi_n, lam_z, nc):
     return out
 
 
+def sheet_profiles(lam_z, n_sheets):
+    """Cumulative profile of each longitudinal colour sheet (the general
+    colour structure rho(x^-, x_T) of Sec. 2 and Sec. 5, one independent
+    transverse charge per slab of the profile).  Reading: sheet s holds the
+    s-th of n_sheets equal-charge slabs of the Gaussian profile, s = 0 at the
+    nucleus' leading edge, so Lambda_s(z) = clip(n Lambda(z) - s, 0, 1) and
+    sum_s Lambda_s = n Lambda."""
+    s = np.arange(n_sheets)[:, None]
+    return np.clip(n_sheets * np.asarray(lam_z)[None, :] - s, 0.0, 1.0)
+
+
+def wilson_line_dag_sheets(phi_sn, lam_z, nc):
+    """Path-ordered V^dagger(z, x_T) = exp(i Lambda_{S-1} phi_{S-1}) ...
+    exp(i Lambda_0 phi_0) for sheet fields phi_sn[s][a][y][x] (reading: the
+    sheet crossed first, s = 0, acts first, i.e. stands rightmost).  The
+    factors no longer commute once the sheets' colour charges differ.
+    One sheet gives wilson_line_dag exactly."""
+    S = phi_sn.shape[0]
+    if S == 1:
+        return wilson_line_dag(phi_sn[0], lam_z, nc)
+    ls = sheet_profiles(lam_z, S)
+    out = None
+    for s in range(S):
+        f = wilson_line_dag(phi_sn[s], ls[s], nc)
+        out = f if out is None else mm(f, out)
+    return out
+
+
 def links_at(p: Params, phi, t_shift):
     """Gauge links of the two superposed nuclei (Sec. 3 Eqs.
     3d_colorfield_1/2) with both nuclei moved by t_shift (0 or -dt) from
@@ -323,8 +352,9 @@ def links_at(p: Params, phi, t_shift):
     z = np.arange(p.nz) * p.a_z
     lam_a = big_lambda(z, za, p.sigma_l, "A")
     lam_b = big_lambda(z, zb, p.sigma_l, "B")
-    vd_a = wilson_line_dag(phi[0], lam_a, nc)
-    vd_b = wilson_line_dag(phi[1], lam_b, nc)
+    ph = phi if phi.ndim == 5 else phi[None]          # [S][N][a][y][x]
+    vd_a = wilson_line_dag_sheets(ph[:, 0], lam_a, nc)
+    vd_b = wilson_line_dag_sheets(ph[:, 1], lam_b, nc)
     U = np.empty((3, p.nz, p.ny, p.nx, nc, nc), complex)
     for i in (0, 1):
         ua = mm(dag(vd_a), shift(vd_a, i, 1))
@@ -358,7 +388,9 @@ def hop_at(n, pq):
 def init_mv(p: Params, rho):
     """MV initial state at t0 (U) and t0 - dt/2 (E, charges).
 
-    rho[N][a][y][x]: transverse MV charges of A (N=0) and B (N=1).
+    rho[N][a][y][x]: transverse MV charges of A (N=0) and B (N=1); with
+    p.n_sheets = S > 1, rho[s][N][a][y][x]: one independent charge per
+    longitudinal colour sheet (wilson_line_dag_sheets).
     Steps: Poisson solve; links at t0 and t0 - dt; E from the exact group
     log of U(t0) U^dagger(t0 - dt) (reading; exactly 0 where the two links
     are bitwise equal); charge density from the discrete Gauss law of
