@@ -424,7 +424,42 @@ def run_extras(G, torch, cfg, args, stream, value):
     out["improved"] = run_improved(G, torch, stream)
     out["ensemble"] = run_ensemble(G, torch, stream)
     out["observables"] = run_observables(G, torch, stream)
+    out["adjoint"] = run_adjoint(G, torch)
     return out
+
+
+def run_adjoint(G, torch, probes=4, h=1e-4):
+    """The differentiated workload (SU(2) 256 x 32^2, 200 steps, FP64): one
+    gradient of the mid-rapidity energy (|z - z_c| < 16a) w.r.t. the MV
+    charges through the hand-written adjoint (checkpoint every 20 steps),
+    timed against the forward alone, and its agreement with central
+    differences at a few random entries."""
+    cfg = dict(gi.CONFIGS["su2_256x32x32"], precision="fp64")
+    n, hw = cfg["steps"], 16.0
+    rho = gi.mv_rho(cfg["seed"], 2, cfg["nx"], cfg["ny"], cfg["g2mu"])
+    G.glasma_adjoint_energy(cfg, rho, 2, hw)            # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    val, _ = G.glasma_adjoint_energy(cfg, rho, n, hw, grad=False)
+    t1 = time.perf_counter()
+    val2, g = G.glasma_adjoint_energy(cfg, rho, n, hw, checkpoint_every=20)
+    t2 = time.perf_counter()
+    rng = np.random.default_rng(1404)
+    errs = []
+    for _ in range(probes):
+        idx = tuple(int(rng.integers(0, s)) for s in rho.shape)
+        rp, rm = rho.copy(), rho.copy()
+        rp[idx] += h
+        rm[idx] -= h
+        fd = (G.glasma_adjoint_energy(cfg, rp, n, hw, grad=False)[0]
+              - G.glasma_adjoint_energy(cfg, rm, n, hw, grad=False)[0]) / (2 * h)
+        errs.append(abs(g[idx] - fd) / abs(fd))
+    return {"workload": "su2_256x32x32 fp64, 200 steps, |z - z_c| < 16",
+            "observable": val, "forward_s": t1 - t0, "forward_and_gradient_s": t2 - t1,
+            "gradient_over_forward": (t2 - t1) / (t1 - t0), "checkpoint_every": 20,
+            "fd_probes": probes, "fd_h": h, "fd_max_rel_err": max(errs),
+            "note": "wall clock through the C ABI from host rho; the 64-entry "
+                    "check is tests/test_gpu_adjoint.py"}
 
 
 def run_observables(G, torch, stream, every=4, steps=200):

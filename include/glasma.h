@@ -80,6 +80,12 @@ typedef struct {
                                iteration also ends when max |dE| stops
                                decreasing within 1024 unit roundoffs of
                                max |E| (the precision's rounding floor) */
+  int n_sheets;             /* longitudinal colour sheets per nucleus
+                               (0 or 1: the single-sheet MV charge; S > 1,
+                               at most 64: S independent transverse charges,
+                               one per equal-charge slab of the profile, each
+                               of std. dev. g2mu / sqrt(S), combined in a
+                               path-ordered Wilson line) */
 } glasma_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both

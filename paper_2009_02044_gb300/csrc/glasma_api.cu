@@ -116,6 +116,7 @@ static int check_params(const glasma_params* p) {
     return set_error(GLASMA_ERR_INVALID_ARG, "precision must be GLASMA_FP64 or GLASMA_FP32");
   if (p->scheme != GLASMA_LEAPFROG && p->scheme != GLASMA_IMPLICIT)
     return set_error(GLASMA_ERR_INVALID_ARG, "scheme must be GLASMA_LEAPFROG or GLASMA_IMPLICIT");
+  if (p->n_sheets < 0 || p->n_sheets > 64) return set_error(GLASMA_ERR_INVALID_ARG, "n_sheets must be 0..64");
   if (p->scheme == GLASMA_IMPLICIT && (p->implicit_max_iter < 1 || !(p->implicit_tol > 0)))
     return set_error(GLASMA_ERR_INVALID_ARG, "implicit scheme needs max_iter >= 1 and tol > 0");
   // both truncated profiles (at t0 and t0 - dt) inside the box

@@ -285,8 +285,8 @@ extern "C" GLASMA_API int glasma_adjoint_energy(const glasma_params* p, const do
                                                 double half_width, int checkpoint_every, void* stream,
                                                 const glasma_allocator* alloc, double* value, double* grad_host) {
   if (!p) return set_error(GLASMA_ERR_INVALID_ARG, "params is NULL");
-  if (p->nc != 2 || p->precision != GLASMA_FP64 || p->scheme != GLASMA_LEAPFROG)
-    return set_error(GLASMA_ERR_INVALID_ARG, "the adjoint covers SU(2), FP64, leapfrog");
+  if (p->nc != 2 || p->precision != GLASMA_FP64 || p->scheme != GLASMA_LEAPFROG || p->n_sheets > 1)
+    return set_error(GLASMA_ERR_INVALID_ARG, "the adjoint covers SU(2), FP64, leapfrog, one colour sheet");
   if (n_steps < 0 || !(half_width > 0.0) || checkpoint_every < 1)
     return set_error(GLASMA_ERR_INVALID_ARG, "need n_steps >= 0, half_width > 0, checkpoint_every >= 1");
   glasma_ctx* c = nullptr;

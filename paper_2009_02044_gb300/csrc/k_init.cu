@@ -15,15 +15,16 @@
 
 namespace glasma {
 
-__global__ void k_philox_rho(double* rho, int na, int nx, int ny, unsigned long long seed, double g2mu) {
-  const int64_t total = (int64_t)2 * na * nx * ny;
+// rho[(s*2 + N)*na + a][y][x] for S sheets; counter (x, y, a, N + 2 s)
+__global__ void k_philox_rho(double* rho, int na, int nx, int ny, int S, unsigned long long seed, double g2mu) {
+  const int64_t total = (int64_t)2 * S * na * nx * ny;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % nx);
     int64_t r = i / nx;
     const int y = (int)(r % ny);
     r /= ny;
     const int a = (int)(r % na);
-    const int N = (int)(r / na);
+    const int N = (int)(r / na);  // N + 2 s
     uint32_t c[4] = {(uint32_t)x, (uint32_t)y, (uint32_t)a, (uint32_t)N};
     philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
     const double u1 = u53(c[0], c[1]), u2 = u53(c[2], c[3]);
@@ -105,13 +106,36 @@ __global__ void k_profile(double* lam, int nz, double a_z, double sigma, double 
   }
 }
 
+// V_N^dagger at transverse site t for the cumulative profile value lam.
+// One sheet: exp(i lam phi_N).  S sheets (phi[(s*2 + N)*na + a][t]): the
+// path-ordered exp(i L_{S-1} phi_{S-1,N}) ... exp(i L_0 phi_{0,N}) with
+// L_s = clip(S lam - s, 0, 1), sheet 0 (the leading slab) acting first.
 template <int NC>
-GL_HD typename Group<NC, double>::M wilson_dag(const double* phi, int N, int na, int64_t nxy, int64_t t, double lam) {
+GL_HD typename Group<NC, double>::M wilson_dag(const double* phi, int N, int na, int64_t nxy, int64_t t, double lam,
+                                               int S = 1) {
   typedef Group<NC, double> G;
-  if (lam == 0.0) return G::ident();
   double v[G::NA];
-  for (int a = 0; a < G::NA; ++a) v[a] = phi[((int64_t)N * na + a) * nxy + t];
-  return G::expi(v, lam);
+  if (S <= 1) {
+    if (lam == 0.0) return G::ident();
+    for (int a = 0; a < G::NA; ++a) v[a] = phi[((int64_t)N * na + a) * nxy + t];
+    return G::expi(v, lam);
+  }
+  typename G::M m = G::ident();
+  bool first = true;
+  for (int s = 0; s < S; ++s) {
+    double ls = (double)S * lam - (double)s;
+    ls = ls < 0.0 ? 0.0 : (ls > 1.0 ? 1.0 : ls);
+    typename G::M f;
+    if (ls == 0.0) {
+      f = G::ident();
+    } else {
+      for (int a = 0; a < G::NA; ++a) v[a] = phi[((int64_t)(s * 2 + N) * na + a) * nxy + t];
+      f = G::expi(v, ls);
+    }
+    m = first ? f : G::mul(f, m);
+    first = false;
+  }
+  return m;
 }
 
 template <int NC>
@@ -133,7 +157,7 @@ GL_HD bool same(const typename Group<NC, double>::M& a, const typename Group<NC,
 template <int NC, typename R>
 __global__ void k_init_links(const double* phi, const double* lam, typename V2T<R>::T* U0,
                              typename V2T<R>::T* U1, typename V2T<R>::T* Uprev, R* E, Geom g, double dt,
-                             int* flag) {
+                             int* flag, int S) {
   typedef Group<NC, double> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
@@ -144,12 +168,12 @@ __global__ void k_init_links(const double* phi, const double* lam, typename V2T<
     M u[2][2];  // [time][direction]
     for (int t = 0; t < 2; ++t) {
       const double la = lam[(t * 2 + 0) * g.nz + n.iz], lb = lam[(t * 2 + 1) * g.nz + n.iz];
-      M vda = wilson_dag<NC>(phi, 0, NA, g.nxy, t0, la);
-      M vdb = wilson_dag<NC>(phi, 1, NA, g.nxy, t0, lb);
+      M vda = wilson_dag<NC>(phi, 0, NA, g.nxy, t0, la, S);
+      M vdb = wilson_dag<NC>(phi, 1, NA, g.nxy, t0, lb, S);
       for (int i = 0; i < 2; ++i) {
         const int64_t tn = i == 0 ? tx : ty;
-        M vda_n = wilson_dag<NC>(phi, 0, NA, g.nxy, tn, la);
-        M vdb_n = wilson_dag<NC>(phi, 1, NA, g.nxy, tn, lb);
+        M vda_n = wilson_dag<NC>(phi, 0, NA, g.nxy, tn, la, S);
+        M vdb_n = wilson_dag<NC>(phi, 1, NA, g.nxy, tn, lb, S);
         M ua = G::d_mul(vda, vda_n);  // V_A(x) V_A^dag(x+i)
         M ub = G::d_mul(vdb, vdb_n);
         u[t][i] = G::mul(ua, ub);
@@ -239,7 +263,8 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
   const glasma_params& p = c->p;
   const int na = c->na;
   const int64_t nxy = c->g.nxy, V = c->g.V;
-  const int F = 2 * na;
+  const int S = p.n_sheets > 1 ? p.n_sheets : 1;
+  const int F = 2 * S * na;
   int st;
   // scratch: rho/phi (real), two complex work arrays, lambda table, rho3, slice max, flag
   double* rho = (double*)ctx_alloc(c, sizeof(double) * F * nxy);
@@ -254,7 +279,8 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
                     "rho upload");
     if (st) return st;
   } else {
-    k_philox_rho<<<grid_for(F * nxy), 256, 0, c->stream>>>(rho, na, p.nx, p.ny, p.seed, p.g2mu);
+    k_philox_rho<<<grid_for(F * nxy), 256, 0, c->stream>>>(rho, na, p.nx, p.ny, S, p.seed,
+                                                            S > 1 ? p.g2mu / sqrt((double)S) : p.g2mu);
   }
   // Poisson: forward DFT x, y; kernel; inverse y, x; real part / (nx ny)
   k_real_to_cplx<<<grid_for(F * nxy), 256, 0, c->stream>>>(rho, w0, F * nxy);
@@ -272,7 +298,7 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
   cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream);
   k_init_links<NC, R><<<grid_for(V, 128), 128, 0, c->stream>>>(
       rho, lam, (typename V2T<R>::T*)c->U[0], (typename V2T<R>::T*)c->U[1], (typename V2T<R>::T*)c->Uprev,
-      (R*)c->E, c->g, p.dt, c->dflag);
+      (R*)c->E, c->g, p.dt, c->dflag, S);
   k_divergence<NC, R><<<p.nz, 256, 0, c->stream>>>((const typename V2T<R>::T*)c->U[0], (const R*)c->E, c->g,
                                                   1.0 / (p.a_t * p.a_t), 1.0 / (p.a_z * p.a_z), rho3, smax);
   st = cuda_check(cudaGetLastError(), "init kernels");
@@ -342,7 +368,7 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
 // F*nx*ny complex values each) and the profile table lam[(t*2 + N)*nz + iz].
 int device_philox_rho(const glasma_params& p, int na, double* rho, cudaStream_t s) {
   const int64_t n = (int64_t)2 * na * p.nx * p.ny;
-  k_philox_rho<<<grid_for(n), 256, 0, s>>>(rho, na, p.nx, p.ny, p.seed, p.g2mu);
+  k_philox_rho<<<grid_for(n), 256, 0, s>>>(rho, na, p.nx, p.ny, 1, p.seed, p.g2mu);
   return cuda_check(cudaGetLastError(), "philox rho");
 }
 

@@ -41,7 +41,7 @@ class glasma_params(C.Structure):
                 ("uv_cutoff", C.c_double), ("z_offset", C.c_double),
                 ("seed", C.c_ulonglong), ("precision", C.c_int),
                 ("scheme", C.c_int), ("implicit_max_iter", C.c_int),
-                ("implicit_tol", C.c_double)]
+                ("implicit_tol", C.c_double), ("n_sheets", C.c_int)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -157,6 +157,7 @@ def make_params(cfg):
     p.scheme = IMPLICIT if sch in ("implicit", IMPLICIT) else LEAPFROG
     p.implicit_max_iter = int(cfg.get("implicit_max_iter", 50))
     p.implicit_tol = float(cfg.get("implicit_tol", 1e-14))
+    p.n_sheets = int(cfg.get("n_sheets", 1))
     return p
 
 
@@ -205,9 +206,11 @@ def glasma_init_mv(cfg, rho=None, stream=None, torch_memory=True):
     if rho is not None:
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         na = p.nc * p.nc - 1
-        if rho.shape != (2, na, p.ny, p.nx):
-            raise ValueError("rho must have shape (2, %d, %d, %d)"
-                             % (na, p.ny, p.nx))
+        want = (2, na, p.ny, p.nx)
+        if p.n_sheets > 1:
+            want = (p.n_sheets,) + want
+        if rho.shape != want:
+            raise ValueError("rho must have shape %s" % (want,))
     keep = None
     alloc_ptr = None
     if torch_memory:

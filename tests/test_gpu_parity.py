@@ -339,3 +339,32 @@ def test_improved_scheme_is_stable_where_leapfrog_grows(G):
     # leapfrog: compare the same phase of its oscillation early and late
     assert np.max(Hl[-3:]) > 1.05 * np.max(Hl[:3])
     assert np.min(Hl[-3:]) > 1.05 * np.min(Hl[1:4])
+
+
+# ---------------------------------------------------------------------------
+# Longitudinal colour structure: several colour sheets per nucleus
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_colour_sheets_match_oracle(G, nc):
+    """Three independent colour sheets per nucleus (path-ordered Wilson
+    line), host charges, through the collision in FP64."""
+    S = 3
+    cfg = dict(gi.small_config(nc, nz=64, nx=7, ny=6, sigma_l=3.0, seed=23), n_sheets=S)
+    rho = gi.mv_rho(23, nc, 7, 6, cfg["g2mu"], sheets=S)
+    p = O.Params.from_dict(cfg)
+    h = G.glasma_init_mv(cfg, rho)
+    compare_state(G, h, O.init_mv(p, rho), TOL64, "sheets init")
+    G.glasma_step(h, 30)
+    compare_state(G, h, O.step(O.init_mv(p, rho), 30), TOL64, "sheets 30 steps")
+
+
+def test_colour_sheets_seed_only_init(G):
+    """The device draw of the sheet charges (counter (x, y, a, N + 2 s))
+    equals the host generator's."""
+    S = 4
+    cfg = dict(gi.small_config(2, nz=64, nx=5, ny=8, sigma_l=3.0, seed=99), n_sheets=S)
+    p = O.Params.from_dict(cfg)
+    h = G.glasma_init_mv(cfg, None)
+    st = O.init_mv(p, gi.mv_rho(99, 2, 5, 8, cfg["g2mu"], sheets=S))
+    compare_state(G, h, st, TOL64, "sheets seed init")
