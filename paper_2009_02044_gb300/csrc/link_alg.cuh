@@ -79,11 +79,9 @@ struct LinkAlg<3, float> {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        cplx<R> acc = cj(y.m[3 * j + i]);
-        acc = acc + mulc(x.m[3 * i], y1.m[3 * j]);
-        acc = acc + mulc(x.m[3 * i + 1], y1.m[3 * j + 1]);
-        acc = acc + mulc(x.m[3 * i + 2], y1.m[3 * j + 2]);
-        r.m[3 * i + j] = acc;
+        cplx<R> acc = fma_cj(x.m[3 * i], y1.m[3 * j], cj(y.m[3 * j + i]));
+        acc = fma_cj(x.m[3 * i + 1], y1.m[3 * j + 1], acc);
+        r.m[3 * i + j] = fma_cj(x.m[3 * i + 2], y1.m[3 * j + 2], acc);
       }
     return r;
   }
@@ -95,11 +93,9 @@ struct LinkAlg<3, float> {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        cplx<R> acc = cj(x.m[3 * j + i]);
-        acc = acc + mulc(y.m[j], x1.m[i]);
-        acc = acc + mulc(y.m[3 + j], x1.m[3 + i]);
-        acc = acc + mulc(y.m[6 + j], x1.m[6 + i]);
-        r.m[3 * i + j] = acc;
+        cplx<R> acc = fma_cj(y.m[j], x1.m[i], cj(x.m[3 * j + i]));
+        acc = fma_cj(y.m[3 + j], x1.m[3 + i], acc);
+        r.m[3 * i + j] = fma_cj(y.m[6 + j], x1.m[6 + i], acc);
       }
     return r;
   }
@@ -228,7 +224,7 @@ struct LinkAlg<3, float> {
     const cplx<R>* b = &x.m[3];
     cplx<R> p = b[0] + cj(ap[1]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p = p + mulc(b[k], ap[k]);
+    for (int k = 0; k < 3; ++k) p = fma_cj(b[k], ap[k], p);
     cplx<R> bb[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) bb[k] = b[k] - p * ap[k];

@@ -36,6 +36,14 @@ template <typename R> GL_HD cplx<R> cj(cplx<R> a) { return {a.re, -a.im}; }
 template <typename R> GL_HD cplx<R> mulc(cplx<R> a, cplx<R> b) {
   return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
 }
+// acc + a*conj(b), four fused multiply-adds
+template <typename R> GL_HD cplx<R> fma_cj(cplx<R> a, cplx<R> b, cplx<R> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.im, b.re, acc.im);
+  acc.im = fma(-a.re, b.im, acc.im);
+  return acc;
+}
 // acc + a*b
 template <typename R> GL_HD cplx<R> fma_c(cplx<R> a, cplx<R> b, cplx<R> acc) {
   acc.re = fma(a.re, b.re, acc.re);
@@ -169,9 +177,8 @@ struct Group<3, R> {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         cplx<R> acc = mulc(x.m[3 * i], y.m[3 * j]);
-        acc = acc + mulc(x.m[3 * i + 1], y.m[3 * j + 1]);
-        acc = acc + mulc(x.m[3 * i + 2], y.m[3 * j + 2]);
-        r.m[3 * i + j] = acc;
+        acc = fma_cj(x.m[3 * i + 1], y.m[3 * j + 1], acc);
+        r.m[3 * i + j] = fma_cj(x.m[3 * i + 2], y.m[3 * j + 2], acc);
       }
     return r;
   }
@@ -183,9 +190,8 @@ struct Group<3, R> {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         cplx<R> acc = mulc(y.m[j], x.m[i]);
-        acc = acc + mulc(y.m[3 + j], x.m[3 + i]);
-        acc = acc + mulc(y.m[6 + j], x.m[6 + i]);
-        r.m[3 * i + j] = acc;
+        acc = fma_cj(y.m[3 + j], x.m[3 + i], acc);
+        r.m[3 * i + j] = fma_cj(y.m[6 + j], x.m[6 + i], acc);
       }
     return r;
   }
