@@ -153,10 +153,15 @@ struct LinkAlg<3, float> {
     proj_mul_sum(u, s, o);
   }
 
-  // exp(i c v^a t^a) - 1 without forming the identity: the series
-  // e = iQ (1 + iQ/2 (1 + iQ/3 (1 + iQ/4))) at Q / 2^s with ||Q||_F / 2^s
-  // <= 1/32 (truncation below 1e-8 of |e|), then s exact doublings
-  // e_{2h} = 2 e_h + e_h^2 (from exp(iQ) = exp(iQ/2)^2).
+  // exp(i c v^a t^a) - 1 by Cayley-Hamilton.  Q = c v^a t^a is hermitian and
+  // traceless, so Q^3 = c1 Q + c0 with c1 = tr(Q^2)/2 and c0 = det Q, and
+  // every power is Q^n = al_n + be_n Q + ga_n Q^2 with
+  //   al_{n+1} = c0 ga_n,  be_{n+1} = al_n + c1 ga_n,  ga_{n+1} = be_n.
+  // exp(iQ) - 1 = sum_{n>=1} (i^n/n!) Q^n = f0 + f1 Q + f2 Q^2, summed to
+  // n = 9: the remainder is below ||Q||^10/10! < 3e-10 ||Q|| for
+  // ||Q||_F <= 1/2.  f0 collects only terms of order ||Q||^3 and up, so
+  // nothing of size 1 is formed.  Larger ||Q|| is halved s times first and
+  // the result doubled exactly, e_{2h} = 2 e_h + e_h^2.
   GL_HD static M expi(const R* v, R c) {
     R nq2 = 0.f;
 #pragma unroll
@@ -165,7 +170,7 @@ struct LinkAlg<3, float> {
     if (nq == 0.f) return G::zero();
     int s = 0;
     R sc = c;
-    while (nq > 0.03125f && s < 40) {
+    while (nq > 0.5f && s < 40) {
       nq *= 0.5f;
       sc *= 0.5f;
       ++s;
@@ -174,26 +179,63 @@ struct LinkAlg<3, float> {
 #pragma unroll
     for (int a = 0; a < NA; ++a) cv[a] = sc * v[a];
     const M Q = G::herm(cv);
-    // Horner: Y <- 1 + (i/k) Q Y for k = 4, 3, 2, then e = i Q Y
-    M Y;
+    // Q^2: real diagonal, upper triangle, lower = conjugate
+    R d2[3];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Y.m[k] = cplx<R>{-0.25f * Q.m[k].im, 0.25f * Q.m[k].re};  // iQ/4
-    Y.m[0].re += 1.f;
-    Y.m[4].re += 1.f;
-    Y.m[8].re += 1.f;
+    for (int i = 0; i < 3; ++i) {
+      R acc = Q.m[4 * i].re * Q.m[4 * i].re;
 #pragma unroll
-    for (int k = 3; k >= 2; --k) {
-      const M QY = G::mul(Q, Y);
-      const R f = 1.f / (R)k;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) Y.m[q] = cplx<R>{-f * QY.m[q].im, f * QY.m[q].re};
-      Y.m[0].re += 1.f;
-      Y.m[4].re += 1.f;
-      Y.m[8].re += 1.f;
+      for (int k = 0; k < 3; ++k)
+        if (k != i) acc = fma(Q.m[3 * i + k].re, Q.m[3 * i + k].re, fma(Q.m[3 * i + k].im, Q.m[3 * i + k].im, acc));
+      d2[i] = acc;
     }
-    M e = G::mul(Q, Y);
+    const cplx<R> q01 = fma_c(Q.m[2], Q.m[7], fma_c(Q.m[1], Q.m[4], Q.m[0].re * Q.m[1]));
+    const cplx<R> q02 = fma_c(Q.m[1], Q.m[5], fma_c(Q.m[2], Q.m[8], Q.m[0].re * Q.m[2]));
+    const cplx<R> q12 = fma_c(Q.m[3], Q.m[2], fma_c(Q.m[5], Q.m[8], Q.m[4].re * Q.m[5]));
+    const R c1 = 0.5f * (d2[0] + d2[1] + d2[2]);
+    // det Q = q00 q11 q22 + 2 Re(Q01 Q12 Q20) - q00 |Q12|^2 - q11 |Q02|^2 - q22 |Q01|^2
+    const cplx<R> t = Q.m[1] * Q.m[5];
+    R c0 = Q.m[0].re * Q.m[4].re * Q.m[8].re;
+    c0 = fma(2.f * t.re, Q.m[2].re, c0);
+    c0 = fma(2.f * t.im, Q.m[2].im, c0);
+    c0 = fma(-Q.m[0].re, Q.m[5].re * Q.m[5].re + Q.m[5].im * Q.m[5].im, c0);
+    c0 = fma(-Q.m[4].re, Q.m[2].re * Q.m[2].re + Q.m[2].im * Q.m[2].im, c0);
+    c0 = fma(-Q.m[8].re, Q.m[1].re * Q.m[1].re + Q.m[1].im * Q.m[1].im, c0);
+    // series: n = 1 gives i Q; n >= 2 by the recurrence
+    R al = 0.f, be = 1.f, ga = 0.f;
+    cplx<R> f0{0.f, 0.f}, f1{0.f, 1.f}, f2{0.f, 0.f};
+    const R inv_fact[10] = {1.f, 1.f, 0.5f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f, 1.f / 720.f, 1.f / 5040.f,
+                            1.f / 40320.f, 1.f / 362880.f};
 #pragma unroll
-    for (int q = 0; q < 9; ++q) e.m[q] = cplx<R>{-e.m[q].im, e.m[q].re};  // times i
+    for (int n = 2; n <= 9; ++n) {
+      const R nal = c0 * ga, nbe = fma(c1, ga, al);
+      ga = be;
+      al = nal;
+      be = nbe;
+      const R k = inv_fact[n];
+      // i^n: n mod 4 = 0: +1, 1: +i, 2: -1, 3: -i
+      if ((n & 3) == 0) {
+        f0.re = fma(k, al, f0.re); f1.re = fma(k, be, f1.re); f2.re = fma(k, ga, f2.re);
+      } else if ((n & 3) == 1) {
+        f0.im = fma(k, al, f0.im); f1.im = fma(k, be, f1.im); f2.im = fma(k, ga, f2.im);
+      } else if ((n & 3) == 2) {
+        f0.re = fma(-k, al, f0.re); f1.re = fma(-k, be, f1.re); f2.re = fma(-k, ga, f2.re);
+      } else {
+        f0.im = fma(-k, al, f0.im); f1.im = fma(-k, be, f1.im); f2.im = fma(-k, ga, f2.im);
+      }
+    }
+    M e;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R qd = Q.m[4 * i].re;
+      e.m[4 * i] = cplx<R>{fma(f2.re, d2[i], fma(f1.re, qd, f0.re)), fma(f2.im, d2[i], fma(f1.im, qd, f0.im))};
+    }
+    e.m[1] = fma_c(f2, q01, f1 * Q.m[1]);
+    e.m[2] = fma_c(f2, q02, f1 * Q.m[2]);
+    e.m[5] = fma_c(f2, q12, f1 * Q.m[5]);
+    e.m[3] = fma_c(f2, cj(q01), f1 * Q.m[3]);
+    e.m[6] = fma_c(f2, cj(q02), f1 * Q.m[6]);
+    e.m[7] = fma_c(f2, cj(q12), f1 * Q.m[7]);
     for (int k = 0; k < s; ++k) {
       const M e2 = G::mul(e, e);
 #pragma unroll
