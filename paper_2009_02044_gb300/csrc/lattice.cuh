@@ -169,22 +169,25 @@ GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const 
   typedef LinkAlg<NC, Rc> G;
   typedef typename G::M M;
   typename G::Sum S = G::zero_sum();
-#pragma unroll
+  const Rc wt = w[0], wz = w[2];
+  // one copy of the staple code (fewer instruction-cache misses)
+#pragma unroll 1
   for (int j = 0; j < 3; ++j) {
     if (j == i) continue;
+    const Rc wj = j == 2 ? wz : wt;
     const bool fwd = (j != 2) || (n.iz <= g.nz - 2);
     const bool bwd = (j != 2) || (n.iz >= 1);
     if (fwd) {
       M T = G::mul_d(LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.p[i]),
                      LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.p[j]));
       T = G::mul_d(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.s));
-      G::sum_add(S, w[j], T);
+      G::sum_add(S, wj, T);
     }
     if (bwd) {
       M T = G::mul(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.m[j]),
                    LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, diag_pm(g, n, i, j)));
       T = G::d_mul(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.m[j]));
-      G::sum_add(S, w[j], T);
+      G::sum_add(S, wj, T);
     }
   }
   constexpr int NA = G::NA;

@@ -166,12 +166,12 @@ struct LinkAlg<3, float> {
     R nq2 = 0.f;
 #pragma unroll
     for (int a = 0; a < NA; ++a) nq2 += v[a] * v[a];
-    R nq = fabsf(c) * gl_sqrt(0.5f * nq2);
-    if (nq == 0.f) return G::zero();
+    R nn = 0.5f * c * c * nq2;  // ||Q||_F^2
+    if (nn == 0.f) return G::zero();
     int s = 0;
     R sc = c;
-    while (nq > 0.5f && s < 40) {
-      nq *= 0.5f;
+    while (nn > 0.25f && s < 40) {
+      nn *= 0.25f;
       sc *= 0.5f;
       ++s;
     }
@@ -248,6 +248,9 @@ struct LinkAlg<3, float> {
   // conj(row0 x row1), every step written for the deviation from e_k so
   // that no O(1) quantity is formed.
   GL_HD static R inv_sqrt_m1(R eps) {  // 1/sqrt(1+eps) - 1
+    // a link one step from the group has |eps| ~ 1e-7: the binomial series
+    // -eps/2 + 3 eps^2/8 - 5 eps^3/16 is exact to 35/128 eps^4 there
+    if (fabsf(eps) < 1e-3f) return eps * fma(eps, fma(eps, -0.3125f, 0.375f), -0.5f);
     const R r = gl_sqrt(1.f + eps);
     return -eps / (r * (1.f + r));
   }
