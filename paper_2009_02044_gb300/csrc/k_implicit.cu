@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(192) k_implicit_prev(ImplArgs<R> a) {
   R e[NA];
 #pragma unroll
   for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
-  typename G::M u = G::mul(G::expi(e, -a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
+  typename G::M u = G::mul(G::expi_series(e, -a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
   if (sizeof(R) == 4) u = G::reunit(u);
   LinkIO<NC, R>::template store<R>(a.Uout, i, a.g.V, s, u);
 }
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
   }
 #pragma unroll
   for (int c = 0; c < NA; ++c) a.Ework[(int64_t)(i * NA + c) * a.g.V + s] = ew[c];
-  M u = G::mul(G::expi(e, a.dt), Ui);
+  M u = G::mul(G::expi_series(e, a.dt), Ui);
   if (sizeof(R) == 4) u = G::reunit(u);
   LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
 }
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
       emax = fmax(emax, fabs((double)e[c]));
       a.E[idx] = e[c];
     }
-    M u = G::mul(G::expi(e, a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
+    M u = G::mul(G::expi_series(e, a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
     if (sizeof(R) == 4) u = G::reunit(u);
     LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
   }

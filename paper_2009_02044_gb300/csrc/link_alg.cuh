@@ -29,6 +29,7 @@ struct LinkAlg<NC, double> : Group<NC, double> {
   typedef Group<NC, double> G;
   typedef typename G::M M;
   static constexpr bool kDelta = false;
+  GL_HD static M expi_series(const double* v, double c) { return G::expi(v, c); }
   typedef M Sum;
   GL_HD static M full(const M& u) { return u; }
   GL_HD static Sum zero_sum() { return G::zero(); }
@@ -244,6 +245,56 @@ struct LinkAlg<3, float> {
     return e;
   }
 
+  // The same exponential by a Taylor-Horner series (kept for the implicit
+  // sweep, whose register budget suits it better): the series
+  // e = iQ (1 + iQ/2 (1 + iQ/3 (1 + iQ/4))) at Q / 2^s with ||Q||_F / 2^s
+  // <= 1/32 (truncation below 1e-8 of |e|), then s exact doublings
+  // e_{2h} = 2 e_h + e_h^2 (from exp(iQ) = exp(iQ/2)^2).
+  GL_HD static M expi_series(const R* v, R c) {
+    R nq2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) nq2 += v[a] * v[a];
+    R nq = fabsf(c) * gl_sqrt(0.5f * nq2);
+    if (nq == 0.f) return G::zero();
+    int s = 0;
+    R sc = c;
+    while (nq > 0.03125f && s < 40) {
+      nq *= 0.5f;
+      sc *= 0.5f;
+      ++s;
+    }
+    R cv[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) cv[a] = sc * v[a];
+    const M Q = G::herm(cv);
+    // Horner: Y <- 1 + (i/k) Q Y for k = 4, 3, 2, then e = i Q Y
+    M Y;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Y.m[k] = cplx<R>{-0.25f * Q.m[k].im, 0.25f * Q.m[k].re};  // iQ/4
+    Y.m[0].re += 1.f;
+    Y.m[4].re += 1.f;
+    Y.m[8].re += 1.f;
+#pragma unroll
+    for (int k = 3; k >= 2; --k) {
+      const M QY = G::mul(Q, Y);
+      const R f = 1.f / (R)k;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Y.m[q] = cplx<R>{-f * QY.m[q].im, f * QY.m[q].re};
+      Y.m[0].re += 1.f;
+      Y.m[4].re += 1.f;
+      Y.m[8].re += 1.f;
+    }
+    M e = G::mul(Q, Y);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) e.m[q] = cplx<R>{-e.m[q].im, e.m[q].re};  // times i
+    for (int k = 0; k < s; ++k) {
+      const M e2 = G::mul(e, e);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) e.m[q] = (R)2 * e.m[q] + e2.m[q];
+    }
+    return e;
+  }
+
   // Re-unitarisation of 1 + d: rows 0 and 1 by Gram-Schmidt, row 2 =
   // conj(row0 x row1), every step written for the deviation from e_k so
   // that no O(1) quantity is formed.
@@ -316,6 +367,7 @@ struct LinkAlg<2, float> {
 
   GL_HD static M ident() { return G::zero(); }
   GL_HD static M full(const M& d) { return M{{d.a.re + 1.f, d.a.im}, d.b}; }
+  GL_HD static M expi_series(const R* v, R c) { return expi(v, c); }
   GL_HD static M dag(const M& x) { return M{cj(x.a), -x.b}; }
   // alpha = a1 + a2 + a1 a2 - b1 b2*, beta = b1 + b2 + a1 b2 + b1 a2*
   GL_HD static M mul(const M& x, const M& y) {
