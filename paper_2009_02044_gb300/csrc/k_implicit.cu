@@ -12,7 +12,8 @@
 //
 // Buffers: Uprev = U(t_{n-1}), U[cur] = U(t_n), the other U buffer and Uit
 // hold the iterates of U(t_{n+1}); E is iterated in place, Ework keeps
-// E(t_{n-1/2}) + dt J.  conv[k] is the largest |E^(k+1) - E^(k)| of
+// E(t_{n-1/2}) + dt J + dt times the force of the two fixed slots (t_n and
+// t_{n-1}), which the prepare kernel evaluates once per step.  conv[k] is the largest |E^(k+1) - E^(k)| of
 // iteration k (atomicMax on the bit pattern of a non-negative double).
 // The iteration ends when that change is below implicit_tol or stops
 // decreasing at the rounding floor of the state's precision (reached first in
@@ -69,9 +70,11 @@ __device__ __forceinline__ const typename V2T<R>::T* slot_buf(const ImplArgs<R>&
   return m == 0 ? a.X : (m == 1 ? a.Un : a.Up);
 }
 
-// Time-averaged force on link i at x.
+// Time-averaged force on link i at x from the time slots m_begin..m_end-1
+// (0: the iterate of t_{n+1}, 1: t_n, 2: t_{n-1}); the force is linear in
+// the slot terms, so the fixed slots 1 and 2 are summed once per step.
 template <int NC, typename R>
-__device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R* F) {
+__device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R* F, int m_begin, int m_end) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
@@ -85,7 +88,7 @@ __device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R*
     const bool fwd = (j != 2) || (n.iz <= a.g.nz - 2);
     const bool bwd = (j != 2) || (n.iz >= 1);
 #pragma unroll 1
-    for (int m = 0; m < 3; ++m) {
+    for (int m = m_begin; m < m_end; ++m) {
       const typename V2T<R>::T* Bi = slot_buf(a, m, zplane, i);
       const typename V2T<R>::T* Bj = slot_buf(a, m, zplane, j);
       typename G::Sum S = G::zero_sum();
@@ -174,6 +177,12 @@ __global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
 #pragma unroll
     for (int c = 0; c < NA; ++c) ew[c] += dj[c];
   }
+  {
+    R F[NA];
+    force_implicit<NC, R>(a, site_nbr_tz(a.g, t, iz), i, F, 1, 3);
+#pragma unroll
+    for (int c = 0; c < NA; ++c) ew[c] += a.dt * F[c];
+  }
 #pragma unroll
   for (int c = 0; c < NA; ++c) a.Ework[(int64_t)(i * NA + c) * a.g.V + s] = ew[c];
   M u = G::mul(G::expi_series(e, a.dt), Ui);
@@ -181,9 +190,15 @@ __global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
   LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
 }
 
-// One fixed-point sweep: E = Ework + dt F(U_{n-1}, U_n, X), Xn = exp(i dt E) U_n.
+// One fixed-point sweep: E = Ework + dt F_0(X), Xn = exp(i dt E) U_n, where
+// Ework already holds E(t_{n-1/2}) + dt J + dt (F_1(U_n) + F_2(U_{n-1})).
+// FP32: 4 blocks of 192 threads per SM (80 registers); FP64 needs the
+// registers of one block per SM instead of spilling.
+template <typename R> struct ImplOcc { static constexpr int blocks = 4; };
+template <> struct ImplOcc<double> { static constexpr int blocks = 1; };
+
 template <int NC, typename R>
-__global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
+__global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplArgs<R> a) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
@@ -198,7 +213,7 @@ __global__ void __launch_bounds__(192, 4) k_implicit_iter(ImplArgs<R> a) {
     const SiteNbr n = site_nbr_tz(a.g, t, iz);
     const int64_t s = n.s;
     R F[NA];
-    force_implicit<NC, R>(a, n, i, F);
+    force_implicit<NC, R>(a, n, i, F, 0, 1);
     R e[NA];
 #pragma unroll
     for (int c = 0; c < NA; ++c) {
