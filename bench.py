@@ -613,9 +613,11 @@ def run_improved(G, torch, stream, steps=10, warm=3):
     H1 = G.glasma_tmunu(h)[1]
     g = G.glasma_gauss_residual(h)
     G.glasma_free(h)
-    # per sweep: read U(n-1), U(n), the iterate, E(n-1/2)+J and E; write E
-    # and the next iterate (FP32 SU(3): 3*216 + 3*96 + 216 bytes per site)
-    sweep_bytes = V * (3 * 216 + 3 * 96 + 216)
+    # per sweep: read U(n) and the iterate, the work field (E(n-1/2) + dt J
+    # + the fixed-slot force) and E; write E and the next iterate
+    # (FP32 SU(3): 2*216 + 3*96 + 216 bytes per site); U(n-1) is read once
+    # per step by the prepare kernel
+    sweep_bytes = V * (2 * 216 + 3 * 96 + 216)
     n_sweeps = sum(iters)
     peak, kind = load_peaks()
     gbs = sweep_bytes * n_sweeps / (total * 1e-3) / 1e9
