@@ -454,10 +454,19 @@ def run_adjoint(G, torch, probes=4, h=1e-4):
         fd = (G.glasma_adjoint_energy(cfg, rp, n, hw, grad=False)[0]
               - G.glasma_adjoint_energy(cfg, rm, n, hw, grad=False)[0]) / (2 * h)
         errs.append(abs(g[idx] - fd) / abs(fd))
-    return {"workload": "su2_256x32x32 fp64, 200 steps, |z - z_c| < 16",
+    # the workload's own precision: FP32 forward and checkpoints, FP64 reverse
+    cfg32 = dict(gi.CONFIGS["su2_256x32x32"], precision="fp32")
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    v32, g32 = G.glasma_adjoint_energy(cfg32, rho, n, hw, checkpoint_every=20)
+    t4 = time.perf_counter()
+    return {"workload": "su2_256x32x32, 200 steps, |z - z_c| < 16",
             "observable": val, "forward_s": t1 - t0, "forward_and_gradient_s": t2 - t1,
             "gradient_over_forward": (t2 - t1) / (t1 - t0), "checkpoint_every": 20,
             "fd_probes": probes, "fd_h": h, "fd_max_rel_err": max(errs),
+            "fp32_forward": {"forward_and_gradient_s": t4 - t3,
+                             "observable_rel_diff": abs(v32 - val) / abs(val),
+                             "grad_max_rel_diff_vs_fp64": float(np.max(np.abs(g32 - g)) / np.max(np.abs(g)))},
             "note": "wall clock through the C ABI from host rho; the 64-entry "
                     "check is tests/test_gpu_adjoint.py"}
 

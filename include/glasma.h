@@ -313,7 +313,7 @@ GLASMA_API int glasma_fit_gaussian(const double* x, const double* f, int n, doub
 
 /*
  * Gradient of the mid-rapidity energy with respect to the initial MV colour
- * charges (SU(2), FP64, leapfrog): the hand-written adjoint of
+ * charges (SU(2), leapfrog, one colour sheet): the hand-written adjoint of
  * glasma_init_mv followed by n_steps glasma_step calls.  The observable is
  *   O = a_z sum_{iz : |iz a_z - z_c| < half_width} eps(iz)
  * with eps(iz) the energy density of glasma_tmunu at step n_steps (Sec. 4)
@@ -323,9 +323,13 @@ GLASMA_API int glasma_fit_gaussian(const double* x, const double* f, int n, doub
  * segment from its checkpoint (device memory: (ceil(n_steps / K) +
  * min(K, n_steps) + 2) states plus about 70 doubles per site, through
  * `alloc` as in glasma_init_mv).  Outputs: *value = O (may be NULL) and
- * grad_host[2][3][ny][nx] = dO/drho (NULL: forward only).  Synchronises
- * the stream.  Errors: INVALID_ARG (not SU(2)/FP64/leapfrog, bad sizes),
- * PARTICLE_EXIT, OOM, CUDA.
+ * grad_host[2][3][ny][nx] = dO/drho (NULL: forward only).  With
+ * p->precision = GLASMA_FP32 the forward run and its checkpoints are FP32
+ * and the reverse pass works in FP64 on those states (converted on the
+ * device), i.e. it differentiates the FP32 trajectory; with GLASMA_FP64
+ * everything is FP64.  Synchronises the stream.  Errors: INVALID_ARG (not
+ * SU(2)/leapfrog, several colour sheets, bad sizes), PARTICLE_EXIT, OOM,
+ * CUDA.
  */
 GLASMA_API int glasma_adjoint_energy(const glasma_params* p, const double* rho_host, int n_steps,
                                      double half_width, int checkpoint_every, void* stream,

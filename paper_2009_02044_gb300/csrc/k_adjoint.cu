@@ -134,7 +134,57 @@ int load_state(glasma_ctx* c, const Sizes& z, const StateRef& src) {
   return st;
 }
 
+// A state in the context's own precision (raw buffers; the pointer types
+// are those of FP64 and are reinterpreted for FP32).
 StateRef alloc_state(Scratch& sc, const glasma_ctx* c) {
+  StateRef r{};
+  const size_t rs = c->rs;
+  r.U = (double2*)sc.get<char>(2 * rs * 3 * 2 * (size_t)c->g.V);
+  r.E = (double*)sc.get<char>(rs * 9 * (size_t)c->g.V);
+  r.QA = (double*)sc.get<char>(rs * 3 * c->QA_cap * (size_t)c->g.nxy);
+  r.QB = (double*)sc.get<char>(rs * 3 * c->QB_cap * (size_t)c->g.nxy);
+  return r;
+}
+
+// FP32 states hold U - 1 (alpha - 1 for SU(2)) and FP32 fields: the reverse
+// pass reads them as FP64 full links and fields.
+__global__ void k_links_to64(const float2* in, double2* out, int64_t V) {
+  GRID_STRIDE(i, 6 * V) {
+    const float2 v = in[i];
+    const bool alpha = ((i / V) & 1) == 0;
+    out[i] = make_double2((double)v.x + (alpha ? 1.0 : 0.0), (double)v.y);
+  }
+}
+
+__global__ void k_reals_to64(const float* in, double* out, int64_t n) {
+  GRID_STRIDE(i, n) out[i] = (double)in[i];
+}
+
+// FP64 view of a state: the raw buffers for an FP64 context, converted
+// copies in `cv` for an FP32 one.
+struct View {
+  const double2* U;
+  const double* E;
+  const double* QA;
+  const double* QB;
+};
+
+View view64(const StateRef& st, bool f32, const StateRef& cv, const glasma_ctx* c, bool links, bool fields,
+            bool charges) {
+  if (!f32) return View{st.U, st.E, st.QA, st.QB};
+  const Geom& g = c->g;
+  cudaStream_t s = c->stream;
+  if (links) k_links_to64<<<grid_of(6 * g.V), 256, 0, s>>>((const float2*)st.U, cv.U, g.V);
+  if (fields) k_reals_to64<<<grid_of(9 * g.V), 256, 0, s>>>((const float*)st.E, cv.E, 9 * g.V);
+  if (charges) {
+    const int64_t na = 3 * (int64_t)c->WA * g.nxy, nb = 3 * (int64_t)c->WB * g.nxy;
+    if (na) k_reals_to64<<<grid_of(na), 256, 0, s>>>((const float*)st.QA, cv.QA, na);
+    if (nb) k_reals_to64<<<grid_of(nb), 256, 0, s>>>((const float*)st.QB, cv.QB, nb);
+  }
+  return View{cv.U, cv.E, cv.QA, cv.QB};
+}
+
+StateRef alloc_state64(Scratch& sc, const glasma_ctx* c) {
   StateRef r{};
   r.U = sc.get<double2>(3 * 2 * (size_t)c->g.V);
   r.E = sc.get<double>(9 * (size_t)c->g.V);
@@ -148,8 +198,10 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
   const glasma_params& p = c->p;
   const Geom g = c->g;
   cudaStream_t s = c->stream;
-  const Sizes z{2 * 8 * 3 * (size_t)c->nv * g.V, 8 * 9 * (size_t)g.V, 8 * 3 * (size_t)c->WA * g.nxy,
-                8 * 3 * (size_t)c->WB * g.nxy};
+  const size_t rs = c->rs;
+  const bool f32 = rs == 4;
+  const Sizes z{2 * rs * 3 * (size_t)c->nv * g.V, rs * 9 * (size_t)g.V, rs * 3 * (size_t)c->WA * g.nxy,
+                rs * 3 * (size_t)c->WB * g.nxy};
   Scratch sc(c);
   const int ncp = n_steps > 0 ? (n_steps + K - 1) / K : 0;
   std::vector<StateRef> ck(ncp);
@@ -158,6 +210,12 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
   std::vector<StateRef> seg(seg_len + 1);
   for (auto& r : seg) r = alloc_state(sc, c);
   StateRef fin = alloc_state(sc, c);  // the final state before the observable's E update
+  // FP64 copies for an FP32 context: state n of a reverse step and E of n+1
+  StateRef cva{}, cvb{};
+  if (f32) {
+    cva = alloc_state64(sc, c);
+    cvb.E = sc.get<double>(9 * (size_t)g.V);
+  }
   double* Ub = sc.get<double>(12 * (size_t)g.V);
   double* Eb = sc.get<double>(9 * (size_t)g.V);
   double* Ebp = sc.get<double>(9 * (size_t)g.V);
@@ -199,12 +257,18 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
   cudaMemsetAsync(Ub, 0, sizeof(double) * 12 * g.V, s);
   cudaMemsetAsync(QAb, 0, z.qa ? z.qa : 8, s);
   cudaMemsetAsync(QBb, 0, z.qb ? z.qb : 8, s);
-  k_adj_obs<<<grid_of(9 * g.V), 256, 0, s>>>(fin.E, (const double*)c->E, wsl, Eb, Ebp, g, ia2t, ia2z);
-  k_adj_plaq<<<grid_of(g.V, 128), 128, 0, s>>>(fin.U, Ebp, p.dt, wsl, G, g, wt, wz, ia2t, ia2z);
+  const View vf = view64(fin, f32, cva, c, true, true, true);
+  const double* Ep = (const double*)c->E;  // E' of the observable's own update
+  if (f32) {
+    k_reals_to64<<<grid_of(9 * g.V), 256, 0, s>>>((const float*)c->E, cvb.E, 9 * g.V);
+    Ep = cvb.E;
+  }
+  k_adj_obs<<<grid_of(9 * g.V), 256, 0, s>>>(vf.E, Ep, wsl, Eb, Ebp, g, ia2t, ia2z);
+  k_adj_plaq<<<grid_of(g.V, 128), 128, 0, s>>>(vf.U, Ebp, p.dt, wsl, G, g, wt, wz, ia2t, ia2z);
   k_adj_gather<<<grid_of(g.V), 256, 0, s>>>(G, Ub, g);
   if (hopN)
     k_adj_hop_current<<<grid_of((int64_t)(g.nz - 1) * g.nxy), 256, 0, s>>>(
-        fin.U, Ebp, fin.QA, fin.QB, QAb, QBb, Ub, fin.zA0, c->WA, fin.zB0, c->WB, g, az2);
+        vf.U, Ebp, vf.QA, vf.QB, QAb, QBb, Ub, fin.zA0, c->WA, fin.zB0, c->WB, g, az2);
   st = cuda_check(cudaGetLastError(), "adjoint observable");
   if (st) return st;
 
@@ -220,13 +284,19 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
     }
     for (int n = n1 - 1; n >= n0 && !st; --n) {
       const int k = n - n0;
+      const View vn = view64(seg[k], f32, cva, c, true, false, true);
+      const double* En = seg[k + 1].E;
+      if (f32) {
+        k_reals_to64<<<grid_of(9 * g.V), 256, 0, s>>>((const float*)seg[k + 1].E, cvb.E, 9 * g.V);
+        En = cvb.E;
+      }
       LinkRevArgs a;
-      a.U = seg[k].U;
-      a.En = seg[k + 1].E;
+      a.U = vn.U;
+      a.En = En;
       a.Ub = Ub;
       a.Eb = Eb;
-      a.QA = seg[k].QA;
-      a.QB = seg[k].QB;
+      a.QA = vn.QA;
+      a.QB = vn.QB;
       a.QAb = QAb;
       a.QBb = QBb;
       a.hop = hop_at(n, c->hop_p, c->hop_q) ? 1 : 0;
@@ -238,7 +308,7 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
       a.dt = p.dt;
       a.az2 = az2;
       k_adj_link<<<grid_of(3 * g.V), 256, 0, s>>>(a);
-      k_adj_plaq<<<grid_of(g.V, 128), 128, 0, s>>>(seg[k].U, Eb, p.dt, nullptr, G, g, wt, wz, ia2t, ia2z);
+      k_adj_plaq<<<grid_of(g.V, 128), 128, 0, s>>>(vn.U, Eb, p.dt, nullptr, G, g, wt, wz, ia2t, ia2z);
       k_adj_gather<<<grid_of(g.V), 256, 0, s>>>(G, Ub, g);
       st = cuda_check(cudaGetLastError(), "adjoint step");
     }
@@ -264,7 +334,8 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
   if (!st) st = device_poisson(p, rho, phi, (int)F, w0, w1, s);
   if (!st) st = device_profile(p, lam, s);
   if (st) return st;
-  k_adj_div<<<grid_of(g.V), 256, 0, s>>>(s0->U, s0->E, QAb, QBb, s0->zA0, c->WA, s0->zB0, c->WB, Eb, Ub, g, ia2t);
+  const View v0 = view64(*s0, f32, cva, c, true, true, false);
+  k_adj_div<<<grid_of(g.V), 256, 0, s>>>(v0.U, v0.E, QAb, QBb, s0->zA0, c->WA, s0->zB0, c->WB, Eb, Ub, g, ia2t);
   k_adj_log<<<grid_of(2 * g.V), 256, 0, s>>>(phi, lam, Eb, Ub, Umb, g, p.dt);
   k_adj_links<<<grid_of(g.V, 128), 128, 0, s>>>(phi, lam, Ub, Umb, phib_z, g);
   k_adj_zsum<<<grid_of(F * nxy), 256, 0, s>>>(phib_z, phib, g);
@@ -285,8 +356,8 @@ extern "C" GLASMA_API int glasma_adjoint_energy(const glasma_params* p, const do
                                                 double half_width, int checkpoint_every, void* stream,
                                                 const glasma_allocator* alloc, double* value, double* grad_host) {
   if (!p) return set_error(GLASMA_ERR_INVALID_ARG, "params is NULL");
-  if (p->nc != 2 || p->precision != GLASMA_FP64 || p->scheme != GLASMA_LEAPFROG || p->n_sheets > 1)
-    return set_error(GLASMA_ERR_INVALID_ARG, "the adjoint covers SU(2), FP64, leapfrog, one colour sheet");
+  if (p->nc != 2 || p->scheme != GLASMA_LEAPFROG || p->n_sheets > 1)
+    return set_error(GLASMA_ERR_INVALID_ARG, "the adjoint covers SU(2), leapfrog, one colour sheet");
   if (n_steps < 0 || !(half_width > 0.0) || checkpoint_every < 1)
     return set_error(GLASMA_ERR_INVALID_ARG, "need n_steps >= 0, half_width > 0, checkpoint_every >= 1");
   glasma_ctx* c = nullptr;
