@@ -255,8 +255,9 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
   st = launch_step_leapfrog(c, hopN);  // E' = E(N + 1/2) in c->E; charges moved in place
   if (st) return st;
   cudaMemsetAsync(Ub, 0, sizeof(double) * 12 * g.V, s);
-  cudaMemsetAsync(QAb, 0, z.qa ? z.qa : 8, s);
-  cudaMemsetAsync(QBb, 0, z.qb ? z.qb : 8, s);
+  // the charge adjoints are FP64 whatever the state's precision
+  cudaMemsetAsync(QAb, 0, sizeof(double) * 3 * c->QA_cap * (size_t)g.nxy, s);
+  cudaMemsetAsync(QBb, 0, sizeof(double) * 3 * c->QB_cap * (size_t)g.nxy, s);
   const View vf = view64(fin, f32, cva, c, true, true, true);
   const double* Ep = (const double*)c->E;  // E' of the observable's own update
   if (f32) {

@@ -80,14 +80,17 @@ def test_adjoint_rejects_what_it_does_not_cover(G):
 def test_fp32_forward_gradient_is_close_to_fp64(G):
     """FP32 forward and checkpoints, FP64 reverse pass on the FP32 states:
     the gradient of the FP32 trajectory, within FP32 rounding of the FP64
-    gradient (1e-4 relative to its largest entry)."""
+    gradient (1e-5 relative to its largest entry; 3e-7 measured after 33
+    steps), and independent of the checkpoint spacing."""
     cfg, n, hw = SMALL[2]
     p = O.Params.from_dict(cfg)
     rho = gi.mv_rho(cfg["seed"], 2, p.nx, p.ny, p.g2mu)
     v64, g64 = G.glasma_adjoint_energy(cfg, rho, n, hw, checkpoint_every=7)
     v32, g32 = G.glasma_adjoint_energy(dict(cfg, precision="fp32"), rho, n, hw, checkpoint_every=7)
     assert abs(v32 - v64) <= 1e-5 * v64
-    assert np.max(np.abs(g32 - g64)) <= 1e-4 * np.max(np.abs(g64))
+    assert np.max(np.abs(g32 - g64)) <= 1e-5 * np.max(np.abs(g64))
+    g32b = G.glasma_adjoint_energy(dict(cfg, precision="fp32"), rho, n, hw, checkpoint_every=1)[1]
+    assert np.array_equal(g32, g32b)
 
 
 def test_central_differences_on_the_differentiated_workload(G):
