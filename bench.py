@@ -92,11 +92,14 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def load_traffic(workload, precision):
+def load_traffic(workload, precision, nz):
     """Per-launch DRAM bytes of the step kernel from the committed ncu
-    summary, valid only if the kernel sources are unchanged since."""
+    summary, valid only for the workload's own lattice and if the kernel
+    sources are unchanged since."""
     path = os.path.join(ROOT, "profiles", "step_traffic.json")
     try:
+        if nz != gi.CONFIGS[workload]["nz"]:
+            return None
         d = json.load(open(path))
         e = d[workload + ":" + precision]
         if e["kernel_hash"] == step_kernel_hash():
@@ -320,7 +323,7 @@ def run_ours(args, cfg):
     alg = V * bytes_per_site(nc, rs) + (hops / K) * qbytes
     peak, peak_kind = load_peaks()
     achieved = alg / (per_launch_ms * 1e-3) / 1e9
-    traffic = load_traffic(args.workload, args.precision)
+    traffic = load_traffic(args.workload, args.precision, cfg["nz"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "kernel": "k_step_leapfrog", "peak_source": peak_kind,
@@ -390,6 +393,24 @@ def run_extras(G, torch, cfg, args, stream, value):
                   "d2h_bytes_per_step": tab.nbytes / K,
                   "what": "glasma_init_mv from host rho + %d steps + "
                           "glasma_tmunu to host, wall clock" % K}
+    # sampling cost, timed apart from the steps: one T^{mu nu}(z) table of
+    # the state (FP64 sums) written to device memory
+    with torch.cuda.stream(stream):
+        hs = G.glasma_init_mv(p, rho_pinned, stream=stream)
+        tab_dev = torch.empty((p["nz"], 4), dtype=torch.float64, device="cuda")
+    G.glasma_step(hs, 3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(20):
+        G.glasma_tmunu_device(hs, tab_dev.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["tmunu_sample"] = {"ms": e0.elapsed_time(e1) / 20,
+                           "what": "one T^{mu nu}(z) sample of the state (k_tmunu, "
+                                   "FP64 sums, device output), timed apart from the steps"}
+    G.glasma_free(hs)
     # FP64 comparison run (same event) and energy-density error
     other = "fp64" if args.precision == "fp32" else "fp32"
     k64 = min(K, 400)
