@@ -540,8 +540,18 @@ def run_observables(G, torch, stream, every=4, steps=200):
                                  az, tt.data_ptr(), eta.data_ptr(), eta.numel(),
                                  out.data_ptr(), coords="milne", stream=stream)
             prof[tau] = (out, tt)      # tt kept alive until the kernel ran
+        # <p_T>(t, z) / <p_T>(0, 0) (the Fig. 5 map) at a few (t, z) points
+        tl = [0.0, 10.0, 10.0, 20.0, 20.0, 30.0, 30.0]
+        zl = [0.0, 0.0, 5.0, 0.0, 10.0, 0.0, 15.0]
+        tt_lab = torch.tensor(tl, dtype=torch.float64, device="cuda")
+        zz_lab = torch.tensor(zl, dtype=torch.float64, device="cuda")
+        pt_lab = torch.empty_like(tt_lab)
+        G.glasma_sample_grid(rest.data_ptr(), n_s, nz, 8, 2, t0, dts, z0, az,
+                             tt_lab.data_ptr(), zz_lab.data_ptr(), len(tl),
+                             pt_lab.data_ptr(), coords="lab", stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize()
+    ptl = pt_lab.cpu().numpy()
     eta_h = eta.cpu().numpy()
     res = {"events": len(cfgs), "samples": n_s, "every_steps": every,
            "analysis_ms": ev0.elapsed_time(ev1),
@@ -556,6 +566,8 @@ def run_observables(G, torch, stream, every=4, steps=200):
         res["fit"] = str(ex)
     res["eps_loc_tau50_every4"] = [float("%.4g" % v) for v in last[::4]]
     res["eta_every4"] = [float("%.3g" % v) for v in eta_h[::4]]
+    res["pT_map_over_pT00"] = {"t": tl, "z": zl,
+                               "value": [float("%.4g" % (v / ptl[0])) for v in ptl]}
     mid = len(eta_h) // 2
     te = [tau * float(prof[tau][0][mid].item()) for tau in taus]
     res["tau_eps_loc_eta0"] = dict(zip([str(t) for t in taus], te))
