@@ -185,8 +185,34 @@ struct TmnArgs {
   double* tab;  // [nz][4]
 };
 
+// ||x - y||_F^2 of two links in the state's representation (for FP32 the
+// deviations from 1, whose difference is that of the links), each entry's
+// difference formed in FP64 (exact for FP32 entries).
+template <int NC, typename R> struct Fro2;
+template <typename R>
+struct Fro2<3, R> {
+  GL_HD static double diff(const typename Group<3, R>::M& x, const typename Group<3, R>::M& y) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double dr = (double)x.m[k].re - (double)y.m[k].re, di = (double)x.m[k].im - (double)y.m[k].im;
+      acc += dr * dr + di * di;
+    }
+    return acc;
+  }
+};
+template <typename R>
+struct Fro2<2, R> {
+  GL_HD static double diff(const typename Group<2, R>::M& x, const typename Group<2, R>::M& y) {
+    const double a = (double)x.a.re - (double)y.a.re, b = (double)x.a.im - (double)y.a.im;
+    const double c = (double)x.b.re - (double)y.b.re, d = (double)x.b.im - (double)y.b.im;
+    return 2.0 * (a * a + b * b + c * c + d * d);
+  }
+};
+
 // Per-site arithmetic in the state's precision R (so E(n+1/2) equals what
-// the step kernel would write), every accumulation in FP64.
+// the step kernel would write; FP32 plaquette products in the deviation
+// form), every accumulation in FP64.
 template <int NC, typename R>
 __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
   typedef LinkAlg<NC, R> G;
@@ -242,38 +268,35 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
       }
       e2[i] = 0.5 * acc / (a.a[i] * a.a[i]);
     }
-    // magnetic terms from the plaquettes at the base site, in FP64:
+    // magnetic terms from the plaquettes at the base site, with the link
+    // products in the state's representation:
     // b_ij = ||U_i(x) U_j(x+i) - U_j(x) U_i(x+j)||_F^2 / (a_i a_j)^2
     // (= 2 (N - Re tr U_ij) for unitary links, without its cancellation),
     // B from Im tr t^a U_ij with U_ij = A B^dagger
-    typedef Group<NC, double> GD;
-    typedef typename GD::M MD;
-    MD ud[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) ud[d] = LinkIO<NC, R>::template load<double>(a.U, d, a.g.V, s);
+    typedef LinkIO<NC, R> IO;
     double bxy, bxz = 0, byz = 0;
     double Bx[NA], By[NA];
     {
-      MD A = GD::mul(ud[0], LinkIO<NC, R>::template load<double>(a.U, 1, a.g.V, n.p[0]));
-      MD B = GD::mul(ud[1], LinkIO<NC, R>::template load<double>(a.U, 0, a.g.V, n.p[1]));
-      bxy = GD::fro2_diff(A, B) / (a.a[0] * a.a[1] * a.a[0] * a.a[1]);
+      const M A = G::mul(Uo[0], IO::template load<R>(a.U, 1, a.g.V, n.p[0]));
+      const M B = G::mul(Uo[1], IO::template load<R>(a.U, 0, a.g.V, n.p[1]));
+      bxy = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[1] * a.a[0] * a.a[1]);
     }
 #pragma unroll
     for (int c = 0; c < NA; ++c) Bx[c] = By[c] = 0.0;
     if (iz <= a.g.nz - 2) {
-      double pr[NA];
-      MD A = GD::mul(ud[0], LinkIO<NC, R>::template load<double>(a.U, 2, a.g.V, n.p[0]));  // U_x U_z(x+x)
-      MD B = GD::mul(ud[2], LinkIO<NC, R>::template load<double>(a.U, 0, a.g.V, n.p[2]));  // U_z U_x(x+z)
-      bxz = GD::fro2_diff(A, B) / (a.a[0] * a.a[2] * a.a[0] * a.a[2]);
-      GD::proj(GD::mul_d(A, B), pr);  // B_y = -2 Im tr t U_zx / (a_z a_x) = +2 Im tr t U_xz / (a_x a_z)
+      R pr[NA];
+      M A = G::mul(Uo[0], IO::template load<R>(a.U, 2, a.g.V, n.p[0]));  // U_x U_z(x+x)
+      M B = G::mul(Uo[2], IO::template load<R>(a.U, 0, a.g.V, n.p[2]));  // U_z U_x(x+z)
+      bxz = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[2] * a.a[0] * a.a[2]);
+      Group<NC, R>::proj(G::mul_d(A, B), pr);  // B_y = -2 Im tr t U_zx / (a_z a_x) = +2 Im tr t U_xz / (a_x a_z)
 #pragma unroll
-      for (int c = 0; c < NA; ++c) By[c] = 2.0 * pr[c] / (a.a[0] * a.a[2]);
-      A = GD::mul(ud[1], LinkIO<NC, R>::template load<double>(a.U, 2, a.g.V, n.p[1]));  // U_y U_z(x+y)
-      B = GD::mul(ud[2], LinkIO<NC, R>::template load<double>(a.U, 1, a.g.V, n.p[2]));  // U_z U_y(x+z)
-      byz = GD::fro2_diff(A, B) / (a.a[1] * a.a[2] * a.a[1] * a.a[2]);
-      GD::proj(GD::mul_d(A, B), pr);  // B_x = -2 Im tr t U_yz / (a_y a_z)
+      for (int c = 0; c < NA; ++c) By[c] = 2.0 * (double)pr[c] / (a.a[0] * a.a[2]);
+      A = G::mul(Uo[1], IO::template load<R>(a.U, 2, a.g.V, n.p[1]));  // U_y U_z(x+y)
+      B = G::mul(Uo[2], IO::template load<R>(a.U, 1, a.g.V, n.p[2]));  // U_z U_y(x+z)
+      byz = Fro2<NC, R>::diff(A, B) / (a.a[1] * a.a[2] * a.a[1] * a.a[2]);
+      Group<NC, R>::proj(G::mul_d(A, B), pr);  // B_x = -2 Im tr t U_yz / (a_y a_z)
 #pragma unroll
-      for (int c = 0; c < NA; ++c) Bx[c] = -2.0 * pr[c] / (a.a[1] * a.a[2]);
+      for (int c = 0; c < NA; ++c) Bx[c] = -2.0 * (double)pr[c] / (a.a[1] * a.a[2]);
     }
     double s_l = 0;
 #pragma unroll
