@@ -112,11 +112,12 @@ __global__ void k_profile(double* lam, int nz, double a_z, double sigma, double 
 // L_s = clip(S lam - s, 0, 1), sheet 0 (the leading slab) acting first.
 template <int NC>
 GL_HD typename Group<NC, double>::M wilson_dag(const double* phi, int N, int na, int64_t nxy, int64_t t, double lam,
-                                               int S = 1) {
+                                               int S = 1, const typename Group<NC, double>::M* full = nullptr) {
   typedef Group<NC, double> G;
   double v[G::NA];
   if (S <= 1) {
     if (lam == 0.0) return G::ident();
+    if (lam == 1.0 && full) return full[(int64_t)N * nxy + t];  // behind the nucleus: exp(i phi), tabulated
     for (int a = 0; a < G::NA; ++a) v[a] = phi[((int64_t)N * na + a) * nxy + t];
     return G::expi(v, lam);
   }
@@ -154,10 +155,24 @@ GL_HD bool same(const typename Group<NC, double>::M& a, const typename Group<NC,
   return true;
 }
 
+// exp(i phi_N(x_T)) for every transverse site, the Wilson line of all the
+// slices a single-sheet nucleus has fully passed (Lambda = 1), computed once.
+template <int NC>
+__global__ void k_wilson_full(const double* phi, typename Group<NC, double>::M* full, int64_t nxy) {
+  typedef Group<NC, double> G;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nxy; i += (int64_t)gridDim.x * blockDim.x) {
+    const int N = (int)(i / nxy);
+    const int64_t t = i - (int64_t)N * nxy;
+    double v[G::NA];
+    for (int a = 0; a < G::NA; ++a) v[a] = phi[((int64_t)N * G::NA + a) * nxy + t];
+    full[i] = G::expi(v, 1.0);
+  }
+}
+
 template <int NC, typename R>
 __global__ void k_init_links(const double* phi, const double* lam, typename V2T<R>::T* U0,
                              typename V2T<R>::T* U1, typename V2T<R>::T* Uprev, R* E, Geom g, double dt,
-                             int* flag, int S) {
+                             int* flag, int S, const typename Group<NC, double>::M* full) {
   typedef Group<NC, double> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
@@ -168,12 +183,12 @@ __global__ void k_init_links(const double* phi, const double* lam, typename V2T<
     M u[2][2];  // [time][direction]
     for (int t = 0; t < 2; ++t) {
       const double la = lam[(t * 2 + 0) * g.nz + n.iz], lb = lam[(t * 2 + 1) * g.nz + n.iz];
-      M vda = wilson_dag<NC>(phi, 0, NA, g.nxy, t0, la, S);
-      M vdb = wilson_dag<NC>(phi, 1, NA, g.nxy, t0, lb, S);
+      M vda = wilson_dag<NC>(phi, 0, NA, g.nxy, t0, la, S, full);
+      M vdb = wilson_dag<NC>(phi, 1, NA, g.nxy, t0, lb, S, full);
       for (int i = 0; i < 2; ++i) {
         const int64_t tn = i == 0 ? tx : ty;
-        M vda_n = wilson_dag<NC>(phi, 0, NA, g.nxy, tn, la, S);
-        M vdb_n = wilson_dag<NC>(phi, 1, NA, g.nxy, tn, lb, S);
+        M vda_n = wilson_dag<NC>(phi, 0, NA, g.nxy, tn, la, S, full);
+        M vdb_n = wilson_dag<NC>(phi, 1, NA, g.nxy, tn, lb, S, full);
         M ua = G::d_mul(vda, vda_n);  // V_A(x) V_A^dag(x+i)
         M ub = G::d_mul(vdb, vdb_n);
         u[t][i] = G::mul(ua, ub);
@@ -296,9 +311,16 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
   const double d = p.z_offset > 0 ? p.z_offset : (ceil(4.0 * p.sigma_l / p.a_z) + 2.0) * p.a_z;
   k_profile<<<grid_for(4 * p.nz), 256, 0, c->stream>>>(lam, p.nz, p.a_z, p.sigma_l, zc + d, zc - d, p.dt);
   cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream);
+  typedef typename Group<NC, double>::M MD;
+  MD* full = nullptr;
+  if (S <= 1) {
+    full = (MD*)ctx_alloc(c, sizeof(MD) * 2 * nxy);
+    if (!full) return set_error(GLASMA_ERR_OOM, "init scratch allocation failed");
+    k_wilson_full<NC><<<grid_for(2 * nxy), 256, 0, c->stream>>>(rho, full, nxy);
+  }
   k_init_links<NC, R><<<grid_for(V, 128), 128, 0, c->stream>>>(
       rho, lam, (typename V2T<R>::T*)c->U[0], (typename V2T<R>::T*)c->U[1], (typename V2T<R>::T*)c->Uprev,
-      (R*)c->E, c->g, p.dt, c->dflag, S);
+      (R*)c->E, c->g, p.dt, c->dflag, S, full);
   k_divergence<NC, R><<<p.nz, 256, 0, c->stream>>>((const typename V2T<R>::T*)c->U[0], (const R*)c->E, c->g,
                                                   1.0 / (p.a_t * p.a_t), 1.0 / (p.a_z * p.a_z), rho3, smax);
   st = cuda_check(cudaGetLastError(), "init kernels");
@@ -354,6 +376,7 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
     c->uprev_valid = true;
   }
   st = cuda_check(cudaStreamSynchronize(c->stream), "init sync 2");
+  ctx_free(c, full);
   ctx_free(c, rho);
   ctx_free(c, w0);
   ctx_free(c, w1);
