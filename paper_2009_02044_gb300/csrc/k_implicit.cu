@@ -78,36 +78,41 @@ __device__ void force_implicit(const ImplArgs<R>& a, const SiteNbr& n, int i, R*
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  const R wt[3] = {R(0.25), R(0.5), R(0.25)};
 #pragma unroll
   for (int c = 0; c < NA; ++c) F[c] = R(0);
+  const int64_t pi = n.p[i];
 #pragma unroll 1
   for (int j = 0; j < 3; ++j) {
     if (j == i) continue;
     const bool zplane = (i == 2) || (j == 2);
     const bool fwd = (j != 2) || (n.iz <= a.g.nz - 2);
     const bool bwd = (j != 2) || (n.iz >= 1);
+    const int64_t pj = n.p[j], mj = n.m[j];
+    const R wj = j == 2 ? a.w[2] : a.w[0];
 #pragma unroll 1
     for (int m = m_begin; m < m_end; ++m) {
       const typename V2T<R>::T* Bi = slot_buf(a, m, zplane, i);
       const typename V2T<R>::T* Bj = slot_buf(a, m, zplane, j);
       typename G::Sum S = G::zero_sum();
       if (fwd) {
-        M T = G::mul_d(LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.p[i]),
-                       LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.p[j]));
+        M T = G::mul_d(LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, pi),
+                       LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, pj));
         T = G::mul_d(T, LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.s));
         G::sum_add(S, R(1), T);
       }
       if (bwd) {
-        M T = G::mul(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.m[j]),
-                     LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, diag_pm(a.g, n, i, j)));
-        T = G::d_mul(T, LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, n.m[j]));
+        // x + e_i - e_j (the wraps of x and y are independent)
+        M T = G::mul(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, mj),
+                     LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, pi + mj - n.s));
+        T = G::d_mul(T, LinkIO<NC, R>::template load<R>(Bj, j, a.g.V, mj));
         G::sum_add(S, R(1), T);
       }
       R pr[NA];
       G::proj_mul_sum(LinkIO<NC, R>::template load<R>(Bi, i, a.g.V, n.s), S, pr);
+      // slot weights 1/4, 1/2, 1/4 for t_{n+1}, t_n, t_{n-1}
+      const R wm = wj * (m == 1 ? R(0.5) : R(0.25));
 #pragma unroll
-      for (int c = 0; c < NA; ++c) F[c] -= a.w[j] * wt[m] * pr[c];
+      for (int c = 0; c < NA; ++c) F[c] -= wm * pr[c];
     }
   }
 }
@@ -131,9 +136,18 @@ __global__ void __launch_bounds__(192) k_implicit_prev(ImplArgs<R> a) {
   LinkIO<NC, R>::template store<R>(a.Uout, i, a.g.V, s, u);
 }
 
-// Hop (charges committed, current into Ework) and the first iterate.
+// Blocks per SM of the prepare and sweep kernels.  FP32: 4 blocks of 192
+// threads (80 registers; the load latency of the staples wants the warps
+// more than the spilled registers cost).  FP64 needs the registers of one
+// block per SM instead of spilling.
+template <typename R> struct ImplOcc { static constexpr int blocks = 4; };
+template <> struct ImplOcc<double> { static constexpr int blocks = 1; };
+
+// Hop (charges committed, current into Ework), the first iterate and the
+// force of the two fixed time slots.  The first iterate is written before
+// the staples, so U_n(x) and E(t_{n-1/2}) are not live across them.
 template <int NC, typename R>
-__global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
+__global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_prep(ImplArgs<R> a) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
@@ -143,71 +157,70 @@ __global__ void __launch_bounds__(192) k_implicit_prep(ImplArgs<R> a) {
   if (t >= (uint32_t)a.g.nxy) return;
   if (i == 2 && iz == a.g.nz - 1) return;
   const int64_t s = (int64_t)iz * a.g.nxy + t;
-  const M Ui = LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s);
-  R e[NA], ew[NA];
-#pragma unroll
-  for (int c = 0; c < NA; ++c) ew[c] = e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
-  if (i == 2 && a.hop) {
-    const int kb = iz - a.zB0;
-    R dj[NA];
-#pragma unroll
-    for (int c = 0; c < NA; ++c) dj[c] = R(0);
-    if (kb >= 0 && kb < a.WB) {
-      R q[NA];
-#pragma unroll
-      for (int c = 0; c < NA; ++c) q[c] = a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
-#pragma unroll
-      for (int c = 0; c < NA; ++c) dj[c] -= a.az2 * q[c];
-      G::adj_dag(Ui, q);
-#pragma unroll
-      for (int c = 0; c < NA; ++c) a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t] = q[c];
-    }
-    const int ka = iz + 1 - a.zA0;
-    if (ka >= 0 && ka < a.WA) {
-      R q[NA];
-#pragma unroll
-      for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
-      G::adj(Ui, q);
-#pragma unroll
-      for (int c = 0; c < NA; ++c) {
-        dj[c] += a.az2 * q[c];
-        a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t] = q[c];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < NA; ++c) ew[c] += dj[c];
-  }
+  R ew[NA];
   {
-    R F[NA];
-    force_implicit<NC, R>(a, site_nbr_tz(a.g, t, iz), i, F, 1, 3);
+    const M Ui = LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s);
+    R e[NA];
 #pragma unroll
-    for (int c = 0; c < NA; ++c) ew[c] += a.dt * F[c];
+    for (int c = 0; c < NA; ++c) ew[c] = e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
+    if (i == 2 && a.hop) {
+      const int kb = iz - a.zB0;
+      R dj[NA];
+#pragma unroll
+      for (int c = 0; c < NA; ++c) dj[c] = R(0);
+      if (kb >= 0 && kb < a.WB) {
+        R q[NA];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) q[c] = a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) dj[c] -= a.az2 * q[c];
+        G::adj_dag(Ui, q);
+#pragma unroll
+        for (int c = 0; c < NA; ++c) a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t] = q[c];
+      }
+      const int ka = iz + 1 - a.zA0;
+      if (ka >= 0 && ka < a.WA) {
+        R q[NA];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
+        G::adj(Ui, q);
+#pragma unroll
+        for (int c = 0; c < NA; ++c) {
+          dj[c] += a.az2 * q[c];
+          a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t] = q[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NA; ++c) ew[c] += dj[c];
+    }
+    // X^(0) = exp(i dt E(t_{n-1/2})) U_n
+    M u = G::mul(G::expi_series(e, a.dt), Ui);
+    if (sizeof(R) == 4) u = G::reunit(u);
+    LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
   }
+  R F[NA];
+  force_implicit<NC, R>(a, site_nbr_tz(a.g, t, iz), i, F, 1, 3);
 #pragma unroll
-  for (int c = 0; c < NA; ++c) a.Ework[(int64_t)(i * NA + c) * a.g.V + s] = ew[c];
-  M u = G::mul(G::expi_series(e, a.dt), Ui);
-  if (sizeof(R) == 4) u = G::reunit(u);
-  LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
+  for (int c = 0; c < NA; ++c) a.Ework[(int64_t)(i * NA + c) * a.g.V + s] = ew[c] + a.dt * F[c];
 }
 
 // One fixed-point sweep: E = Ework + dt F_0(X), Xn = exp(i dt E) U_n, where
 // Ework already holds E(t_{n-1/2}) + dt J + dt (F_1(U_n) + F_2(U_{n-1})).
-// FP32: 4 blocks of 192 threads per SM (80 registers); FP64 needs the
-// registers of one block per SM instead of spilling.
-template <typename R> struct ImplOcc { static constexpr int blocks = 4; };
-template <> struct ImplOcc<double> { static constexpr int blocks = 1; };
-
 template <int NC, typename R>
 __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplArgs<R> a) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
   if (a.k > 0 && implicit_converged(a.conv, a.maxit, a.k - 1, a.tol, sizeof(R) == 4)) return;
-  __shared__ double smax[6], semax[6];
+  // The maxima are taken in the state's precision (the largest change of
+  // an FP32 field, rounded once to FP32, is all the convergence test needs)
+  // and converted to FP64 once per block: per-element FP64 arithmetic would
+  // occupy GB300's narrow FP64 pipe.
+  __shared__ R smax[6], semax[6];
   const int i = (int)threadIdx.y;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const int iz = (int)blockIdx.y;
-  double dmax = 0.0, emax = 0.0;
+  R dmax = R(0), emax = R(0);
   const bool live = t < (uint32_t)a.g.nxy && !(i == 2 && iz == a.g.nz - 1);
   if (live) {
     const SiteNbr n = site_nbr_tz(a.g, t, iz);
@@ -219,9 +232,9 @@ __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplA
     for (int c = 0; c < NA; ++c) {
       const int64_t idx = (int64_t)(i * NA + c) * a.g.V + s;
       e[c] = a.Ework[idx] + a.dt * F[c];
-      const double d = fabs((double)e[c] - (double)a.E[idx]);
-      dmax = isfinite(d) ? fmax(dmax, d) : INFINITY;
-      emax = fmax(emax, fabs((double)e[c]));
+      const R d = fabs(e[c] - a.E[idx]);
+      dmax = isfinite(d) ? fmax(dmax, d) : R(INFINITY);
+      emax = fmax(emax, fabs(e[c]));
       a.E[idx] = e[c];
     }
     M u = G::mul(G::expi_series(e, a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
@@ -241,13 +254,13 @@ __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplA
   }
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    double m = smax[0], me = semax[0];
+    R m = smax[0], me = semax[0];
     for (int w = 1; w < (int)(blockDim.x * blockDim.y) / 32; ++w) {
       m = fmax(m, smax[w]);
       me = fmax(me, semax[w]);
     }
-    atomicMax((unsigned long long*)&a.conv[a.k], (unsigned long long)__double_as_longlong(m));
-    atomicMax((unsigned long long*)&a.conv[a.maxit + 1 + a.k], (unsigned long long)__double_as_longlong(me));
+    atomicMax((unsigned long long*)&a.conv[a.k], (unsigned long long)__double_as_longlong((double)m));
+    atomicMax((unsigned long long*)&a.conv[a.maxit + 1 + a.k], (unsigned long long)__double_as_longlong((double)me));
   }
 }
 

@@ -30,16 +30,6 @@ GL_HD int64_t site_index(const Geom& g, int ix, int iy, int iz) {
   return ((int64_t)iz * g.ny + iy) * g.nx + ix;
 }
 
-// site x + dx e_x + dy e_y + dz e_z (periodic in x, y; caller checks z)
-GL_HD int64_t shifted(const Geom& g, int ix, int iy, int iz, int dx, int dy, int dz) {
-  int x = ix + dx, y = iy + dy;
-  if (x < 0) x += g.nx;
-  if (x >= g.nx) x -= g.nx;
-  if (y < 0) y += g.ny;
-  if (y >= g.ny) y -= g.ny;
-  return site_index(g, x, y, iz + dz);
-}
-
 template <int NC, typename R> struct LinkIO;
 
 // FP32 storage holds U - 1 (see link_alg.cuh); loading it as FP64 gives the
@@ -147,14 +137,6 @@ GL_HD SiteNbr site_nbr_tz(const Geom& g, uint32_t t, int iz) {
   return n;
 }
 
-// Index of x + e_i - e_j for i != j.
-GL_HD int64_t diag_pm(const Geom& g, const SiteNbr& n, int i, int j) {
-  int d[3] = {0, 0, 0};
-  d[i] += 1;
-  d[j] -= 1;
-  return shifted(g, n.ix, n.iy, n.iz, d[0], d[1], d[2]);
-}
-
 // F^a = -sum_{j != i} w_j [Im tr t^a U_{i,j}(x) + Im tr t^a U_{i,-j}(x)]
 // (Sec. 3, Eq. lattice_1 with Eq. plaquette; w_j = 2 / a_j^2), plaquettes
 // that leave the open z range omitted, evaluated from the staple sum:
@@ -170,6 +152,7 @@ GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const 
   typedef typename G::M M;
   typename G::Sum S = G::zero_sum();
   const Rc wt = w[0], wz = w[2];
+  const int64_t pi = n.p[i];
   // one copy of the staple code (fewer instruction-cache misses)
 #pragma unroll 1
   for (int j = 0; j < 3; ++j) {
@@ -177,16 +160,19 @@ GL_HD void link_force_staple(const typename V2T<Rs>::T* U, const Geom& g, const 
     const Rc wj = j == 2 ? wz : wt;
     const bool fwd = (j != 2) || (n.iz <= g.nz - 2);
     const bool bwd = (j != 2) || (n.iz >= 1);
+    const int64_t pj = n.p[j], mj = n.m[j];
     if (fwd) {
-      M T = G::mul_d(LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.p[i]),
-                     LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.p[j]));
+      M T = G::mul_d(LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, pi),
+                     LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, pj));
       T = G::mul_d(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.s));
       G::sum_add(S, wj, T);
     }
     if (bwd) {
-      M T = G::mul(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, n.m[j]),
-                   LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, diag_pm(g, n, i, j)));
-      T = G::d_mul(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, n.m[j]));
+      // x + e_i - e_j: the periodic wraps of x and y depend only on ix and
+      // iy and z has no wrap, so the two offsets add
+      M T = G::mul(LinkIO<NC, Rs>::template load<Rc>(U, i, g.V, mj),
+                   LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, pi + mj - n.s));
+      T = G::d_mul(T, LinkIO<NC, Rs>::template load<Rc>(U, j, g.V, mj));
       G::sum_add(S, wj, T);
     }
   }
