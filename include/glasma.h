@@ -188,10 +188,13 @@ GLASMA_API int glasma_tmunu_device(glasma_ctx* c, double* dev_out);
  * Inputs are device pointers in the library's layout (x fastest, site
  * s = (iz*ny + iy)*nx + ix, V = nz*ny*nx; R = double for GLASMA_FP64,
  * float for GLASMA_FP32):
- *   U  links, complex component k of link d at U[(d*NV + k)*V + s] as
- *      (re, im) pairs of R; SU(2): NV = 2, (alpha, beta) of
- *      [[alpha, beta], [-beta*, alpha*]]; SU(3): NV = 9, row-major 3x3;
- *      in FP32 the stored matrix is U - 1 (alpha - 1 for SU(2)), in FP64
+ *   U  links, complex component k of link d at site s as (re, im) pairs
+ *      of R.  SU(2): k = 0, 1 for (alpha, beta) of
+ *      [[alpha, beta], [-beta*, alpha*]], at U[(d*2 + k)*V + s].
+ *      SU(3): k = 0..8 for the row-major 3x3 entries, in blocks of 32
+ *      sites: U[((d*C + s/32)*9 + k)*32 + s%32] with C = ceil(V/32)
+ *      (the array holds 3*9*32*C pairs; the padding is not read).
+ *      In FP32 the stored matrix is U - 1 (alpha - 1 for SU(2)), in FP64
  *      it is U;
  *   E  fields, E[(d*(nc^2-1) + a)*V + s];
  *   QA, QB charge windows of zA0.. zA0+WA-1 and zB0.. zB0+WB-1 (z slices),

@@ -183,7 +183,7 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
   c->g.V = c->g.nxy * p->nz;
   c->rs = p->precision == GLASMA_FP64 ? 8 : 4;
   hop_ratio(p->dt, p->a_z, &c->hop_p, &c->hop_q);
-  const size_t ub = 2 * c->rs * 3 * (size_t)c->nv * c->g.V;
+  const size_t ub = link_bytes(c);
   const size_t eb = c->rs * 3 * (size_t)c->na * c->g.V;
   c->U[0] = ctx_alloc(c, ub);
   c->U[1] = ctx_alloc(c, ub);
@@ -204,6 +204,17 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
       (p->scheme == GLASMA_IMPLICIT && (!c->Uprev || !c->Uit || !c->Ework || !c->conv))) {
     glasma_free(c);
     return set_error(GLASMA_ERR_OOM, "state allocation failed");
+  }
+  if (link_elems(p->nc, c->g.V) != (int64_t)3 * c->nv * c->g.V) {
+    // SU(3) pads the last block of 32 sites of each direction: zero it, so
+    // state blobs hold no uninitialised bytes
+    void* lb[4] = {c->U[0], c->U[1], c->Uprev, c->Uit};
+    for (int k = 0; k < 4 && !st; ++k)
+      if (lb[k]) st = cuda_check(cudaMemsetAsync(lb[k], 0, ub, c->stream), "link padding clear");
+    if (st) {
+      glasma_free(c);
+      return st;
+    }
   }
   st = run_init(c, rho_host);
   if (st) {
@@ -346,7 +357,7 @@ extern "C" {
 
 // device link array (storage precision) -> host doubles [3][V][NV][2]
 static int links_to_host(glasma_ctx* c, const void* dev, std::vector<double>& out) {
-  const size_t n = 3 * (size_t)c->nv * c->g.V * 2;
+  const size_t n = 2 * (size_t)link_elems(c->p.nc, c->g.V);
   out.resize(n);
   if (c->rs == 8) {
     std::vector<double> raw;
@@ -408,8 +419,9 @@ int glasma_get_fields(glasma_ctx* c, double* U, double* E, double* QA, double* Q
     for (int d = 0; d < 3; ++d)
       for (int64_t s = 0; s < V; ++s) {
         for (int k = 0; k < nv; ++k) {
-          comp[2 * k] = raw[(((size_t)d * nv + k) * V + s) * 2];
-          comp[2 * k + 1] = raw[(((size_t)d * nv + k) * V + s) * 2 + 1];
+          const size_t at = 2 * (size_t)link_index(nc, d, k, V, s);
+          comp[2 * k] = raw[at];
+          comp[2 * k + 1] = raw[at + 1];
         }
         link_to_matrix(c, comp, U + ((size_t)d * V + s) * nc * nc * 2);
       }
@@ -443,14 +455,15 @@ int glasma_get_fields(glasma_ctx* c, double* U, double* E, double* QA, double* Q
 static int upload_links(glasma_ctx* c, void* dev, const double* U) {
   const int64_t V = c->g.V;
   const int nc = c->p.nc, nv = c->nv;
-  std::vector<double> raw(3 * (size_t)nv * V * 2);
+  std::vector<double> raw(2 * (size_t)link_elems(nc, V), 0.0);
   double comp[18];
   for (int d = 0; d < 3; ++d)
     for (int64_t s = 0; s < V; ++s) {
       matrix_to_link(c, U + ((size_t)d * V + s) * nc * nc * 2, comp);
       for (int k = 0; k < nv; ++k) {
-        raw[(((size_t)d * nv + k) * V + s) * 2] = comp[2 * k];
-        raw[(((size_t)d * nv + k) * V + s) * 2 + 1] = comp[2 * k + 1];
+        const size_t at = 2 * (size_t)link_index(nc, d, k, V, s);
+        raw[at] = comp[2 * k];
+        raw[at + 1] = comp[2 * k + 1];
       }
     }
   return reals_to_dev(c, dev, raw.data(), raw.size());
@@ -568,7 +581,7 @@ struct StateHeader {
 };
 
 static size_t blob_arrays(const glasma_ctx* c, size_t sizes[5]) {
-  const size_t ub = 2 * c->rs * 3 * (size_t)c->nv * c->g.V;
+  const size_t ub = link_bytes(c);
   sizes[0] = ub;
   sizes[1] = c->rs * 3 * (size_t)c->na * c->g.V;
   sizes[2] = c->rs * (size_t)c->na * c->WA * c->g.nxy;
@@ -595,7 +608,7 @@ int glasma_get_state(glasma_ctx* c, void* host_buf, size_t bytes) {
   StateHeader h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, "GLASMA01", 8);
-  h.version = 1;
+  h.version = 2;  // 2: SU(3) links in blocks of 32 sites
   h.nc = c->p.nc;
   h.nz = c->g.nz;
   h.nx = c->g.nx;
@@ -637,7 +650,7 @@ int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes) {
   cudaSetDevice(c->device);
   StateHeader h;
   memcpy(&h, host_buf, sizeof(h));
-  if (memcmp(h.magic, "GLASMA01", 8) != 0 || h.version != 1)
+  if (memcmp(h.magic, "GLASMA01", 8) != 0 || h.version != 2)
     return set_error(GLASMA_ERR_INVALID_ARG, "not a glasma state blob");
   if (crc32(&h, offsetof(StateHeader, header_crc)) != h.header_crc)
     return set_error(GLASMA_ERR_CHECKSUM, "state header checksum mismatch");
@@ -713,7 +726,7 @@ int glasma_get_info(const glasma_ctx* c, glasma_info* info) {
   info->window_a[1] = c->WA;
   info->window_b[0] = c->zB0;
   info->window_b[1] = c->WB;
-  info->state_device_bytes = 2 * (2 * c->rs * 3 * (size_t)c->nv * c->g.V) + c->rs * 3 * (size_t)c->na * c->g.V +
+  info->state_device_bytes = 2 * link_bytes(c) + c->rs * 3 * (size_t)c->na * c->g.V +
                              c->rs * (size_t)c->na * (c->QA_cap + c->QB_cap) * c->g.nxy;
   info->kernel_launches = c->last_launches;
   info->implicit_iters = c->last_iters;

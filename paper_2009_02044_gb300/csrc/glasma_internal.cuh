@@ -54,6 +54,9 @@ int cuda_check(cudaError_t e, const char* what);
 void* ctx_alloc(glasma_ctx* c, size_t bytes);
 void ctx_free(glasma_ctx* c, void* p);
 
+// bytes of one link array of the context (all three directions)
+inline size_t link_bytes(const glasma_ctx* c) { return 2 * (size_t)c->rs * (size_t)link_elems(c->p.nc, c->g.V); }
+
 // number of hops after m steps: floor(m p/q + 1/2) in integers
 GL_HD long long hop_count(long long m, long long p, long long q) {
   return (2 * m * p + q) / (2 * q);

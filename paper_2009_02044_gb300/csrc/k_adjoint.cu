@@ -200,7 +200,7 @@ int adjoint_run(glasma_ctx* c, const double* rho_host, int n_steps, double half_
   cudaStream_t s = c->stream;
   const size_t rs = c->rs;
   const bool f32 = rs == 4;
-  const Sizes z{2 * rs * 3 * (size_t)c->nv * g.V, rs * 9 * (size_t)g.V, rs * 3 * (size_t)c->WA * g.nxy,
+  const Sizes z{link_bytes(c), rs * 9 * (size_t)g.V, rs * 3 * (size_t)c->WA * g.nxy,
                 rs * 3 * (size_t)c->WB * g.nxy};
   Scratch sc(c);
   const int ncp = n_steps > 0 ? (n_steps + K - 1) / K : 0;

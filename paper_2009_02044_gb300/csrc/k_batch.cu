@@ -579,7 +579,7 @@ GLASMA_API int glasma_batch_tune(glasma_batch* b, int steps, int* block_sites, i
   for (size_t e = 0; e < ne && !st; ++e) {
     glasma_ctx* c = b->ev[e];
     Snap& s = snap[e];
-    s.bytes[0] = 2 * c->rs * 3 * (size_t)c->nv * c->g.V;
+    s.bytes[0] = link_bytes(c);
     s.bytes[1] = c->rs * 3 * (size_t)c->na * c->g.V;
     s.bytes[2] = c->rs * (size_t)c->na * c->WA * c->g.nxy;
     s.bytes[3] = c->rs * (size_t)c->na * c->WB * c->g.nxy;

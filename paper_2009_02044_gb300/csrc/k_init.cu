@@ -369,7 +369,7 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
   st = cuda_check(cudaGetLastError(), "window fill");
   if (st) return st;
   if (c->Uit) {  // second iterate buffer of the implicit scheme: identity last-slice z links
-    st = cuda_check(cudaMemcpyAsync(c->Uit, c->U[0], 2 * c->rs * 3 * (size_t)c->nv * V, cudaMemcpyDeviceToDevice,
+    st = cuda_check(cudaMemcpyAsync(c->Uit, c->U[0], link_bytes(c), cudaMemcpyDeviceToDevice,
                                     c->stream),
                     "iterate buffer init");
     if (st) return st;

@@ -3,9 +3,14 @@
 //
 // Layout in device memory (V = nz*ny*nx sites, site s = (iz*ny + iy)*nx + ix,
 // x fastest; x, y periodic, z open):
-//   links  U[(d*NV + k)*V + s]   complex component k of link d at site s,
-//                                stored as float2 / double2
-//                                (SU(2): k = alpha, beta; SU(3): row-major 3x3)
+//   links  complex component k of link d at site s, stored as float2 /
+//          double2:
+//          SU(2) (k = alpha, beta): U[(d*2 + k)*V + s];
+//          SU(3) (k = row-major 3x3 entry), in blocks of 32 sites:
+//          U[((d*C + s/32)*9 + k)*32 + s%32] with C = ceil(V/32) blocks per
+//          direction, so the components of one link sit 32 entries apart
+//          (immediate address offsets) and a warp still reads 32
+//          consecutive sites of one component;
 //   fields E[(d*NA + a)*V + s]   algebra component a of E_d at site s
 //   charges Q[(a*W + w)*nxy + t] component a, window slot w, transverse t
 // The z link of the last slice does not exist: it is stored as the identity
@@ -25,6 +30,15 @@ struct Geom {
   int nx, ny, nz;
   int64_t nxy, V;
 };
+
+// Element index of complex component k of link d at site s (see above),
+// and the number of complex elements of one link array (SU(3) pads V up to
+// whole blocks of 32 sites).
+GL_HD int64_t link_index(int nc, int d, int k, int64_t V, int64_t s) {
+  if (nc == 2) return (int64_t)(d * 2 + k) * V + s;
+  return (((int64_t)d * ((V + 31) >> 5) + (s >> 5)) * 9 + k) * 32 + (s & 31);
+}
+GL_HD int64_t link_elems(int nc, int64_t V) { return nc == 2 ? 6 * V : 27 * 32 * ((V + 31) >> 5); }
 
 GL_HD int64_t site_index(const Geom& g, int ix, int iy, int iz) {
   return ((int64_t)iz * g.ny + iy) * g.nx + ix;
@@ -66,9 +80,10 @@ struct LinkIO<3, R> {
   template <typename Rc>
   GL_HD static typename Group<3, Rc>::M load(const typename V2T<R>::T* U, int d, int64_t V, int64_t s) {
     typename Group<3, Rc>::M m;
+    const typename V2T<R>::T* p = U + link_index(3, d, 0, V, s);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      typename V2T<R>::T v = U[(int64_t)(d * 9 + k) * V + s];
+      typename V2T<R>::T v = p[k * 32];
       m.m[k] = cplx<Rc>{Rc(v.x), Rc(v.y)};
     }
     if (DeltaConv<R, Rc>::to_full) {
@@ -81,12 +96,13 @@ struct LinkIO<3, R> {
   template <typename Rc>
   GL_HD static void store(typename V2T<R>::T* U, int d, int64_t V, int64_t s, const typename Group<3, Rc>::M& m) {
     const Rc one = DeltaConv<R, Rc>::to_full ? Rc(1) : Rc(0);
+    typename V2T<R>::T* p = U + link_index(3, d, 0, V, s);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       typename V2T<R>::T v;
       v.x = R(k % 4 == 0 ? m.m[k].re - one : m.m[k].re);
       v.y = R(m.m[k].im);
-      U[(int64_t)(d * 9 + k) * V + s] = v;
+      p[k * 32] = v;
     }
   }
 };

@@ -32,8 +32,10 @@ def G():
 
 def _device_layout(G, h, dtype):
     """Copy a context's fields (via glasma_get_fields) into caller-owned
-    torch device tensors in the library's structure-of-arrays layout; the
-    charge windows cover the whole lattice."""
+    torch device tensors in the library's layout (SU(2) links and all
+    fields as structure of arrays, SU(3) links in blocks of 32 sites with
+    the nine components of a block stored one after another); the charge
+    windows cover the whole lattice."""
     import torch
     p = h.params
     nc, na = p.nc, p.nc * p.nc - 1
@@ -44,8 +46,11 @@ def _device_layout(G, h, dtype):
         U = U - np.eye(nc)
     if nc == 2:
         comp = np.stack([U[..., 0, 0], U[..., 0, 1]], axis=1)   # [3][2][V]
-    else:
-        comp = np.moveaxis(U.reshape(3, V, 9), 2, 1)            # [3][9][V]
+    else:                                                       # [3][C][9][32]
+        C = (V + 31) // 32
+        pad = np.zeros((3, C * 32, 9), dtype=complex)
+        pad[:, :V] = U.reshape(3, V, 9)
+        comp = np.moveaxis(pad.reshape(3, C, 32, 9), 3, 2)
     u = np.stack([comp.real, comp.imag], axis=-1)
     e = np.moveaxis(E.reshape(3, V, na), 2, 1)                  # [3][na][V]
     qa = np.moveaxis(QA.reshape(p.nz, p.ny * p.nx, na), 2, 0)   # [na][nz][nxy]
