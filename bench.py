@@ -492,86 +492,107 @@ def run_adjoint(G, torch, probes=4, h=1e-4):
                     "check is tests/test_gpu_adjoint.py"}
 
 
-def run_observables(G, torch, stream, every=4, steps=200):
-    """The Sec. 4 analysis chain on the 24-event ensemble: the events run
-    through the collision as one batch, T^{mu nu}(z) of every event is
-    sampled on the device every `every` steps, then the event mean, the
-    local rest frame, eps_loc on hyperbolae of constant tau and the
-    Gaussian width in eta_s.  The nuclei (truncated at 4 sigma_L = 24
-    cells) recede along the light cone, so the profile is read where
-    tau exp(-|eta_s|) exceeds that."""
-    cfgs = gi.ensemble_configs()
-    c0 = cfgs[0]
-    nz, dt, az = c0["nz"], c0["dt"], c0.get("a_z", 1.0)
-    n_s = steps // every + 1
-    hs = []
-    with torch.cuda.stream(stream):
-        for c in cfgs:
-            hs.append(G.glasma_init_mv(c, None, stream=stream))
-        tabs = torch.zeros((len(cfgs), n_s, nz, 4), dtype=torch.float64,
-                           device="cuda")
-    b = G.glasma_batch_create(hs)
-    for k in range(n_s):
-        if k:
-            G.glasma_batch_step(b, every)
-        for e, h in enumerate(hs):
-            G.glasma_tmunu_device(h, tabs[e, k].data_ptr())
-    torch.cuda.synchronize()
-    b.close()
-    for h in hs:
-        G.glasma_free(h)
-    # collision origin: the nuclei start at z_c -/+ d and meet at t = d
-    d = (math.ceil(4 * c0["sigma_l"] / az) + 2) * az
-    t0, dts, z0 = -d, every * dt, -nz * az / 2.0
-    taus = [40.0, 45.0, 50.0]
-    with torch.cuda.stream(stream):
-        rest = torch.empty((n_s * nz, 8), dtype=torch.float64, device="cuda")
-        eta = torch.linspace(-0.7, 0.7, 57, dtype=torch.float64, device="cuda")
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        G.glasma_rest_frame(tabs.data_ptr(), len(cfgs), n_s * nz,
-                            rest.data_ptr(), stream)
-        prof = {}
-        for tau in taus:
-            tt = torch.full_like(eta, tau)
-            out = torch.empty_like(eta)
-            G.glasma_sample_grid(rest.data_ptr(), n_s, nz, 8, 4, t0, dts, z0,
-                                 az, tt.data_ptr(), eta.data_ptr(), eta.numel(),
-                                 out.data_ptr(), coords="milne", stream=stream)
-            prof[tau] = (out, tt)      # tt kept alive until the kernel ran
-        # <p_T>(t, z) / <p_T>(0, 0) (the Fig. 5 map) at a few (t, z) points
-        tl = [0.0, 10.0, 10.0, 20.0, 20.0, 30.0, 30.0]
-        zl = [0.0, 0.0, 5.0, 0.0, 10.0, 0.0, 15.0]
-        tt_lab = torch.tensor(tl, dtype=torch.float64, device="cuda")
-        zz_lab = torch.tensor(zl, dtype=torch.float64, device="cuda")
-        pt_lab = torch.empty_like(tt_lab)
-        G.glasma_sample_grid(rest.data_ptr(), n_s, nz, 8, 2, t0, dts, z0, az,
-                             tt_lab.data_ptr(), zz_lab.data_ptr(), len(tl),
-                             pt_lab.data_ptr(), coords="lab", stream=stream)
-        ev1.record(stream)
+def run_observables(G, torch, stream, ms=(0.1, 0.2, 0.4), events=8, every=8,
+                    taus=(12.0, 16.0, 20.0), eta_max=1.2):
+    """The Sec. 4 analysis chain in the regime of the paper's rapidity-
+    profile study (glasma_inputs.thin_ensemble_configs: SU(2), sigma_L =
+    a_T, g^2 mu a_T = 0.4, a_z = a_T/8).  For each IR regulator m, `events`
+    events run through the collision as one batch and T^{mu nu}(z) of every
+    event is sampled on the device every `every` steps; then the event
+    mean, the local rest frame, eps_loc(tau, eta_s) on hyperbolae of
+    constant tau, the Gaussian width sigma_eta (Fig. 4 quotes widths that
+    shrink as m grows) and the free-streaming check tau eps_loc = const at
+    eta_s = 0 (Eq. late_time_energy).  The <p_T>(t, z) map of Fig. 5 is
+    sampled for the smallest m.  The points of the hyperbolae stay at
+    t - z = tau exp(-|eta_s|) >= 3.6 a_T behind the receding nuclei, whose
+    charge ends 4 sigma_L = 4 a_T behind their centres."""
+    res = {"workload": "su2_768x64x64_thin: a_z = a_T/8, dt = a_z/2, sigma_L = a_T, g2mu = 0.4",
+           "events_per_m": events, "every_steps": every, "taus": list(taus),
+           "eta_range": [-eta_max, eta_max], "by_m": {}}
+    analysis_ms = 0.0
+    for m in ms:
+        cfgs = gi.thin_ensemble_configs(m, events)
+        c0 = cfgs[0]
+        nz, dt, az = c0["nz"], c0["dt"], c0["a_z"]
+        n_s = c0["steps"] // every + 1
+        hs = []
+        with torch.cuda.stream(stream):
+            for c in cfgs:
+                hs.append(G.glasma_init_mv(c, None, stream=stream))
+            tabs = torch.zeros((len(cfgs), n_s, nz, 4), dtype=torch.float64,
+                               device="cuda")
+        b = G.glasma_batch_create(hs)
+        for k in range(n_s):
+            if k:
+                G.glasma_batch_step(b, every)
+            for e, h in enumerate(hs):
+                G.glasma_tmunu_device(h, tabs[e, k].data_ptr())
         torch.cuda.synchronize()
-    ptl = pt_lab.cpu().numpy()
-    eta_h = eta.cpu().numpy()
-    res = {"events": len(cfgs), "samples": n_s, "every_steps": every,
-           "analysis_ms": ev0.elapsed_time(ev1),
-           "valid_fraction": float(rest[:, 7].mean().item())}
-    last = prof[taus[-1]][0].cpu().numpy()
-    try:
-        amp, mu, sig = G.glasma_fit_gaussian(eta_h, last, 0.0)
-        res["sigma_eta_tau50"] = sig
-        res["mu_eta_tau50"] = mu
-    except G.GlasmaError as ex:
-        res["sigma_eta_tau50"] = None
-        res["fit"] = str(ex)
-    res["eps_loc_tau50_every4"] = [float("%.4g" % v) for v in last[::4]]
-    res["eta_every4"] = [float("%.3g" % v) for v in eta_h[::4]]
-    res["pT_map_over_pT00"] = {"t": tl, "z": zl,
-                               "value": [float("%.4g" % (v / ptl[0])) for v in ptl]}
-    mid = len(eta_h) // 2
-    te = [tau * float(prof[tau][0][mid].item()) for tau in taus]
-    res["tau_eps_loc_eta0"] = dict(zip([str(t) for t in taus], te))
-    res["free_streaming_spread"] = (max(te) - min(te)) / (sum(te) / len(te))
+        b.close()
+        for h in hs:
+            G.glasma_free(h)
+        # collision origin: the nuclei start at z_c -/+ d and meet at t = d
+        d = (math.ceil(4 * c0["sigma_l"] / az) + 2) * az
+        t0, dts, z0 = -d, every * dt, -nz * az / 2.0
+        with torch.cuda.stream(stream):
+            rest = torch.empty((n_s * nz, 8), dtype=torch.float64, device="cuda")
+            eta = torch.linspace(-eta_max, eta_max, 25, dtype=torch.float64,
+                                 device="cuda")
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            G.glasma_rest_frame(tabs.data_ptr(), len(cfgs), n_s * nz,
+                                rest.data_ptr(), stream)
+            prof = {}
+            for tau in taus:
+                tt = torch.full_like(eta, tau)
+                out = torch.empty_like(eta)
+                G.glasma_sample_grid(rest.data_ptr(), n_s, nz, 8, 4, t0, dts, z0,
+                                     az, tt.data_ptr(), eta.data_ptr(),
+                                     eta.numel(), out.data_ptr(), coords="milne",
+                                     stream=stream)
+                prof[tau] = (out, tt)      # tt kept alive until the kernel ran
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        analysis_ms += ev0.elapsed_time(ev1)
+        eta_h = eta.cpu().numpy()
+        mid = len(eta_h) // 2
+        r = {"valid_fraction": float(rest[:, 7].mean().item()), "sigma_eta": {},
+             "mu_eta": {}}
+        for tau in taus:
+            f = prof[tau][0].cpu().numpy()
+            try:
+                _, mu, sig = G.glasma_fit_gaussian(eta_h, f, 0.1)
+                r["sigma_eta"][str(tau)] = sig
+                r["mu_eta"][str(tau)] = mu
+            except G.GlasmaError as ex:
+                r["sigma_eta"][str(tau)] = None
+                r["fit_error"] = str(ex)
+        last = prof[taus[-1]][0].cpu().numpy()
+        r["eps_loc_tau%g" % taus[-1]] = [float("%.4g" % v) for v in last[::3]]
+        r["eta"] = [float("%.3g" % v) for v in eta_h[::3]]
+        te = [tau * float(prof[tau][0][mid].item()) for tau in taus]
+        r["tau_eps_loc_eta0"] = dict(zip([str(t) for t in taus], te))
+        r["free_streaming_spread"] = (max(te) - min(te)) / (sum(te) / len(te))
+        if m == ms[0]:
+            # <p_T>(t, z) / <p_T>(0, 0) (the Fig. 5 map) at a few (t, z) points
+            tl = [0.0, 2.0, 2.0, 4.0, 4.0, 8.0, 8.0, 16.0, 16.0]
+            zl = [0.0, 0.0, 1.0, 0.0, 2.0, 0.0, 4.0, 0.0, 8.0]
+            with torch.cuda.stream(stream):
+                tt_lab = torch.tensor(tl, dtype=torch.float64, device="cuda")
+                zz_lab = torch.tensor(zl, dtype=torch.float64, device="cuda")
+                pt_lab = torch.empty_like(tt_lab)
+                G.glasma_sample_grid(rest.data_ptr(), n_s, nz, 8, 2, t0, dts, z0,
+                                     az, tt_lab.data_ptr(), zz_lab.data_ptr(),
+                                     len(tl), pt_lab.data_ptr(), coords="lab",
+                                     stream=stream)
+                torch.cuda.synchronize()
+            ptl = pt_lab.cpu().numpy()
+            res["pT_map_over_pT00"] = {
+                "m": m, "t": tl, "z": zl,
+                "value": [float("%.4g" % (v / ptl[0])) for v in ptl]}
+        res["by_m"][str(m)] = r
+    res["analysis_ms"] = analysis_ms
     return res
 
 

@@ -71,6 +71,18 @@ def ensemble_configs():
     return out
 
 
+def thin_ensemble_configs(m_ir, events=8, nc=2, nt=64, nz=768, seed0=5000):
+    """Independent MV events in the regime of the paper's rapidity-profile
+    study (Sec. 4: SU(2), nuclei thin against the transverse scales, the IR
+    regulator well below g^2 mu): a_T = 1, a_z = a_T/8, dt = a_z/2,
+    sigma_L = a_T (8 cells), g^2 mu a_T = 0.4, transverse nt^2, N_L = nz
+    (96 a_T, so both nuclei stay inside the box until t = 40 a_T after
+    the collision)."""
+    return [_cfg(nc=nc, nz=nz, nx=nt, ny=nt, a_z=0.125, dt=0.0625,
+                 sigma_l=1.0, g2mu=0.4, m_ir=float(m_ir), seed=seed0 + e,
+                 steps=704, precision="fp32") for e in range(events)]
+
+
 def small_config(nc, nz=48, nx=12, ny=10, sigma_l=2.0, steps=40, seed=7,
                  **kw):
     """A small collision whose nuclei meet within `steps` steps: used for

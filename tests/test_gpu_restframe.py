@@ -158,3 +158,60 @@ def test_collision_chain_matches_oracle(G):
     ref_prof = RF.interp_tz(ref["eps_loc"], t0, dts, z0, p.a_z, tt, zz)
     assert np.all(np.isfinite(ref_prof))
     assert np.max(np.abs(got_prof - ref_prof)) <= 1e-9 * np.max(ref_prof)
+
+
+def _profiles(G, m, events, nt, taus, eta):
+    """eps_loc(tau, eta_s) of an ensemble of thin-nucleus SU(2) events
+    (glasma_inputs.thin_ensemble_configs) through the library's chain:
+    batched steps, device T^{mu nu} samples, rest frame, Milne sampling."""
+    import math
+    import torch
+    cfgs = gi.thin_ensemble_configs(m, events, nt=nt)
+    c0 = cfgs[0]
+    nz, dt, az, every = c0["nz"], c0["dt"], c0["a_z"], 8
+    n_s = c0["steps"] // every + 1
+    hs = [G.glasma_init_mv(c, None) for c in cfgs]
+    tabs = torch.zeros((events, n_s, nz, 4), dtype=torch.float64, device="cuda")
+    b = G.glasma_batch_create(hs)
+    for k in range(n_s):
+        if k:
+            G.glasma_batch_step(b, every)
+        for e, h in enumerate(hs):
+            G.glasma_tmunu_device(h, tabs[e, k].data_ptr())
+    torch.cuda.synchronize()
+    b.close()
+    for h in hs:
+        G.glasma_free(h)
+    d = (math.ceil(4 * c0["sigma_l"] / az) + 2) * az
+    rest = torch.empty((n_s * nz, 8), dtype=torch.float64, device="cuda")
+    G.glasma_rest_frame(tabs.data_ptr(), events, n_s * nz, rest.data_ptr(),
+                        torch.cuda.current_stream())
+    e_d = _dev(eta)
+    out = {}
+    for tau in taus:
+        t_d = _dev(np.full_like(eta, tau))
+        o = torch.empty_like(e_d)
+        G.glasma_sample_grid(rest.data_ptr(), n_s, nz, 8, 4, -d, every * dt,
+                             -nz * az / 2.0, az, t_d.data_ptr(), e_d.data_ptr(),
+                             len(eta), o.data_ptr(), coords="milne")
+        torch.cuda.synchronize()
+        out[tau] = o.cpu().numpy()
+    return out
+
+
+def test_rapidity_profiles_in_the_papers_regime(G):
+    """Sec. 4 (Fig. 4, Eq. late_time_energy) on thin SU(2) nuclei: the
+    rest-frame energy density is a Gaussian in eta_s centred at 0, it
+    narrows as the IR regulator m grows, and tau eps_loc at eta_s = 0 is
+    independent of tau (free streaming)."""
+    eta = np.linspace(-1.2, 1.2, 25)
+    taus = (12.0, 16.0, 20.0)
+    sig = {}
+    for m in (0.1, 0.4):
+        prof = _profiles(G, m, 4, 64, taus, eta)
+        amp, mu, s = G.glasma_fit_gaussian(eta, prof[20.0], 0.1)
+        assert abs(mu) < 0.15
+        sig[m] = s
+        te = [tau * prof[tau][12] for tau in taus]
+        assert (max(te) - min(te)) / np.mean(te) < 0.05
+    assert sig[0.4] < 0.9 * sig[0.1]
