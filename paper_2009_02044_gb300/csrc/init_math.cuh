@@ -71,15 +71,45 @@ GL_HD void jacobi_herm3(cplx<double>* A, cplx<double>* V) {
 // with eigen-phases in (-pi/2, pi/2)).  S = (W - W^+)/(2i) shares W's
 // eigenvectors and has eigenvalues sin(theta); theta_k = atan2(v^+ S v,
 // v^+ C v) with C = (W + W^+)/2.  Returns false if a phase is outside.
+// Close to the identity (|S|_F < 1/4, so every |theta_k| < 0.253) H is
+// the arcsine series of S instead, arcsin x = sum_k c_k x^(2k+1) with
+// c_k / c_(k-1) = (2k-1)^2 / (2k (2k+1)), summed until a term is below
+// 1e-18 |S|: the link changes of one time step at the initial state are
+// of this kind, and the series costs a few matrix products where the
+// Jacobi sweeps cost many.
 GL_HD bool log_su3(const Group<3, double>::M& W, double* h) {
   cplx<double> S[9], C[9], Vm[9];
+  double sn2 = 0.0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       cplx<double> w = W.m[3 * i + j], wt = cj(W.m[3 * j + i]);
       cplx<double> d = w - wt, s = w + wt;
       S[3 * i + j] = cplx<double>{0.5 * d.im, -0.5 * d.re};  // d / (2i)
       C[3 * i + j] = 0.5 * s;
+      sn2 += S[3 * i + j].re * S[3 * i + j].re + S[3 * i + j].im * S[3 * i + j].im;
     }
+  if (sn2 < 0.0625) {
+    typedef Group<3, double> G;
+    G::M Sm, S2, T, H;
+    for (int m = 0; m < 9; ++m) Sm.m[m] = S[m];
+    S2 = G::mul(Sm, Sm);
+    T = Sm;
+    H = Sm;
+    const double stop = 1e-36 * sn2;
+    for (int k = 1; k < 40; ++k) {
+      const double r = (double)((2 * k - 1) * (2 * k - 1)) / (double)(2 * k * (2 * k + 1));
+      T = G::mul(T, S2);
+      double t2 = 0.0;
+      for (int m = 0; m < 9; ++m) {
+        T.m[m] = r * T.m[m];
+        H.m[m] = H.m[m] + T.m[m];
+        t2 += T.m[m].re * T.m[m].re + T.m[m].im * T.m[m].im;
+      }
+      if (t2 <= stop) break;
+    }
+    G::from_herm(H, h);
+    return true;
+  }
   cplx<double> A[9];
   for (int m = 0; m < 9; ++m) A[m] = S[m];
   jacobi_herm3(A, Vm);

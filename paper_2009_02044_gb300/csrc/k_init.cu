@@ -181,18 +181,34 @@ __global__ void k_init_links(const double* phi, const double* lam, typename V2T<
     const int64_t t0 = s % g.nxy;
     const int64_t tx = n.p[0] % g.nxy, ty = n.p[1] % g.nxy;
     M u[2][2];  // [time][direction]
-    for (int t = 0; t < 2; ++t) {
-      const double la = lam[(t * 2 + 0) * g.nz + n.iz], lb = lam[(t * 2 + 1) * g.nz + n.iz];
-      M vda = wilson_dag<NC>(phi, 0, NA, g.nxy, t0, la, S, full);
-      M vdb = wilson_dag<NC>(phi, 1, NA, g.nxy, t0, lb, S, full);
+    // A nucleus whose Lambda is 0 on this slice (ahead of it) contributes
+    // the identity, and a slice whose Lambdas are the same at t0 and
+    // t0 - dt has the same links at both times (E = 0 there).  Before the
+    // collision at most one nucleus has Lambda > 0 on a slice, so most
+    // slices need one product per link.
+    const double lt[2][2] = {{lam[0 * g.nz + n.iz], lam[1 * g.nz + n.iz]},
+                             {lam[2 * g.nz + n.iz], lam[3 * g.nz + n.iz]}};
+    const bool moving = lt[0][0] != lt[1][0] || lt[0][1] != lt[1][1];
+    for (int t = 0; t < (moving ? 2 : 1); ++t) {
+      const double la = lt[t][0], lb = lt[t][1];
+      const bool ha = la != 0.0, hb = lb != 0.0;
+      M vda = G::ident(), vdb = G::ident();
+      if (ha) vda = wilson_dag<NC>(phi, 0, NA, g.nxy, t0, la, S, full);
+      if (hb) vdb = wilson_dag<NC>(phi, 1, NA, g.nxy, t0, lb, S, full);
       for (int i = 0; i < 2; ++i) {
         const int64_t tn = i == 0 ? tx : ty;
-        M vda_n = wilson_dag<NC>(phi, 0, NA, g.nxy, tn, la, S, full);
-        M vdb_n = wilson_dag<NC>(phi, 1, NA, g.nxy, tn, lb, S, full);
-        M ua = G::d_mul(vda, vda_n);  // V_A(x) V_A^dag(x+i)
-        M ub = G::d_mul(vdb, vdb_n);
-        u[t][i] = G::mul(ua, ub);
+        M m = G::ident();
+        if (ha) m = G::d_mul(vda, wilson_dag<NC>(phi, 0, NA, g.nxy, tn, la, S, full));  // V_A(x) V_A^dag(x+i)
+        if (hb) {
+          const M ub = G::d_mul(vdb, wilson_dag<NC>(phi, 1, NA, g.nxy, tn, lb, S, full));
+          m = ha ? G::mul(m, ub) : ub;
+        }
+        u[t][i] = m;
       }
+    }
+    if (!moving) {
+      u[1][0] = u[0][0];
+      u[1][1] = u[0][1];
     }
     for (int i = 0; i < 2; ++i) {
       double h[NA];
@@ -235,7 +251,12 @@ __global__ void __launch_bounds__(256) k_divergence(const typename V2T<R>::T* U,
       for (int c = 0; c < NA; ++c) dv[c] += w * (double)E[(int64_t)(i * NA + c) * g.V + s];
       if (i == 2 && iz == 0) continue;
       double q[NA];
-      for (int c = 0; c < NA; ++c) q[c] = (double)E[(int64_t)(i * NA + c) * g.V + n.m[i]];
+      bool nz = false;
+      for (int c = 0; c < NA; ++c) {
+        q[c] = (double)E[(int64_t)(i * NA + c) * g.V + n.m[i]];
+        nz = nz || q[c] != 0.0;
+      }
+      if (!nz) continue;  // the transported field is zero (E vanishes off the nuclei)
       typename G::M um = LinkIO<NC, R>::template load<double>(U, i, g.V, n.m[i]);
       G::adj_dag(um, q);
       for (int c = 0; c < NA; ++c) dv[c] -= w * q[c];

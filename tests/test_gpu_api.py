@@ -110,3 +110,20 @@ def test_zero_steps_and_vacuum(G):
     assert np.array_equal(U0, U1) and not np.any(E1) and not np.any(QA)
     tab, H = G.glasma_tmunu(h)
     assert H == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_device_tmunu_table_equals_host_table(G, precision):
+    """glasma_tmunu_device writes the same [nz][4] table as glasma_tmunu,
+    bit for bit (SU(3) on a lattice whose site count is not a multiple of
+    the 32-site link blocks)."""
+    import torch
+    cfg = dict(gi.small_config(3, nx=7, ny=5), precision=precision)
+    assert (cfg["nz"] * cfg["nx"] * cfg["ny"]) % 32 != 0
+    h = G.glasma_init_mv(cfg, None)
+    G.glasma_step(h, 30)
+    dev = torch.full((cfg["nz"], 4), float("nan"), dtype=torch.float64, device="cuda")
+    G.glasma_tmunu_device(h, dev.data_ptr())
+    torch.cuda.synchronize()
+    tab, H = G.glasma_tmunu(h)
+    assert np.array_equal(dev.cpu().numpy(), np.asarray(tab))
