@@ -77,9 +77,13 @@ typedef struct {
   int scheme;               /* GLASMA_LEAPFROG or GLASMA_IMPLICIT */
   int implicit_max_iter;    /* fixed-point iterations of the implicit scheme */
   double implicit_tol;      /* its convergence threshold on max |dE|; the
-                               iteration also ends when max |dE| stops
-                               decreasing within 1024 unit roundoffs of
-                               max |E| (the precision's rounding floor) */
+                               iteration also ends when the contraction
+                               bound d c / (1 - c) (d = max |dE|, c the
+                               larger of the last two ratios of d, below
+                               1/2) is at most 8 unit roundoffs of max |E|,
+                               or when max |dE| stops decreasing within
+                               1024 unit roundoffs of max |E| (the
+                               precision's rounding floor) */
   int n_sheets;             /* longitudinal colour sheets per nucleus
                                (0 or 1: the single-sheet MV charge; S > 1,
                                at most 64: S independent transverse charges,
