@@ -199,8 +199,9 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
   c->red_cap = (size_t)sms * 4 * 8 + 64;
   c->red = (double*)ctx_alloc(c, sizeof(double) * c->red_cap);
   c->tab = (double*)ctx_alloc(c, sizeof(double) * 4 * p->nz);
+  c->tpart = (double*)ctx_alloc(c, sizeof(double) * 5 * kTmunuSplit * p->nz);
   c->dflag = (int*)ctx_alloc(c, sizeof(int) * 8);
-  if (!c->U[0] || !c->U[1] || !c->E || !c->red || !c->tab || !c->dflag ||
+  if (!c->U[0] || !c->U[1] || !c->E || !c->red || !c->tab || !c->tpart || !c->dflag ||
       (p->scheme == GLASMA_IMPLICIT && (!c->Uprev || !c->Uit || !c->Ework || !c->conv))) {
     glasma_free(c);
     return set_error(GLASMA_ERR_OOM, "state allocation failed");

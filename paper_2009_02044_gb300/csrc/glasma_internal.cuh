@@ -36,6 +36,7 @@ struct glasma_ctx {
   double* red = nullptr;      // reduction partials
   size_t red_cap = 0;         // doubles
   double* tab = nullptr;      // [nz][4] T^{mu nu} table
+  double* tpart = nullptr;    // [nz][kTmunuSplit][5] T^{mu nu} block partials
   int* dflag = nullptr;       // device status word(s)
   int last_launches = 0;
   int last_iters = 0;
@@ -47,6 +48,9 @@ struct glasma_ctx {
 };
 
 namespace glasma {
+
+// blocks per z slice of the T^{mu nu} kernel, at most
+constexpr int kTmunuSplit = 8;
 
 // status helpers (defined in glasma_api.cu)
 int set_error(int status, const std::string& msg);

@@ -182,7 +182,8 @@ struct TmnArgs {
   double a[3];
   int hop;
   int zA0, WA, zB0, WB;
-  double* tab;  // [nz][4]
+  int split;     // blocks per z slice
+  double* part;  // [nz][split][5] block sums of eps, p_L, p_T, S_L, non-finite count
 };
 
 // ||x - y||_F^2 of two links in the state's representation (for FP32 the
@@ -212,7 +213,9 @@ struct Fro2<2, R> {
 
 // Per-site arithmetic in the state's precision R (so E(n+1/2) equals what
 // the step kernel would write; FP32 plaquette products in the deviation
-// form), every accumulation in FP64.
+// form), every accumulation in FP64.  Block (iz, p) takes the sites
+// t = p*256 + threadIdx.x + k*split*256 of slice iz; k_tmunu_fold adds the
+// split block sums of a slice in a fixed order.
 template <int NC, typename R>
 __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
   typedef LinkAlg<NC, R> G;
@@ -221,14 +224,38 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
   __shared__ double sh[5][kRedThreads];
   const int iz = blockIdx.x;
   double eps = 0, pl = 0, pt = 0, sl = 0, bad = 0;
-  for (int t = threadIdx.x; t < a.g.nxy; t += blockDim.x) {
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < a.g.nxy; t += a.split * blockDim.x) {
     const int64_t s = (int64_t)iz * a.g.nxy + t;
     SiteNbr n = site_nbr(a.g, s);
-    M Uo[3];
+    typedef LinkIO<NC, R> IO;
+    // magnetic terms from the plaquettes at the base site, with the link
+    // products in the state's representation:
+    // b_ij = ||U_i(x) U_j(x+i) - U_j(x) U_i(x+j)||_F^2 / (a_i a_j)^2
+    // (= 2 (N - Re tr U_ij) for unitary links, without its cancellation),
+    // B from Im tr t^a U_ij with U_ij = A B^dagger.  They come first, so that
+    // only the projections (in the state's precision) stay live across the
+    // three link forces below.
+    double bxy, bxz = 0, byz = 0;
+    R prx[NA], pry[NA];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) Uo[d] = LinkIO<NC, R>::template load<R>(a.U, d, a.g.V, s);
+    for (int c = 0; c < NA; ++c) prx[c] = pry[c] = R(0);
+    {
+      const M A = G::mul(IO::template load<R>(a.U, 0, a.g.V, s), IO::template load<R>(a.U, 1, a.g.V, n.p[0]));
+      const M B = G::mul(IO::template load<R>(a.U, 1, a.g.V, s), IO::template load<R>(a.U, 0, a.g.V, n.p[1]));
+      bxy = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[1] * a.a[0] * a.a[1]);
+    }
+    if (iz <= a.g.nz - 2) {
+      M A = G::mul(IO::template load<R>(a.U, 0, a.g.V, s), IO::template load<R>(a.U, 2, a.g.V, n.p[0]));  // U_x U_z(x+x)
+      M B = G::mul(IO::template load<R>(a.U, 2, a.g.V, s), IO::template load<R>(a.U, 0, a.g.V, n.p[2]));  // U_z U_x(x+z)
+      bxz = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[2] * a.a[0] * a.a[2]);
+      Group<NC, R>::proj(G::mul_d(A, B), pry);  // B_y = -2 Im tr t U_zx / (a_z a_x) = +2 Im tr t U_xz / (a_x a_z)
+      A = G::mul(IO::template load<R>(a.U, 1, a.g.V, s), IO::template load<R>(a.U, 2, a.g.V, n.p[1]));  // U_y U_z(x+y)
+      B = G::mul(IO::template load<R>(a.U, 2, a.g.V, s), IO::template load<R>(a.U, 1, a.g.V, n.p[2]));  // U_z U_y(x+z)
+      byz = Fro2<NC, R>::diff(A, B) / (a.a[1] * a.a[2] * a.a[1] * a.a[2]);
+      Group<NC, R>::proj(G::mul_d(A, B), prx);  // B_x = -2 Im tr t U_yz / (a_y a_z)
+    }
     double e2[3] = {0, 0, 0};
-    double eb[2][NA];
+    double s_l = 0;
     const int ilast = (iz == a.g.nz - 1) ? 2 : 3;
     for (int i = 0; i < ilast; ++i) {
       R F[NA];
@@ -252,7 +279,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
           R q[NA];
 #pragma unroll
           for (int c = 0; c < NA; ++c) q[c] = a.QA[((int64_t)c * a.WA + ka) * a.g.nxy + t];
-          G::adj(Uo[2], q);
+          G::adj(IO::template load<R>(a.U, 2, a.g.V, s), q);
 #pragma unroll
           for (int c = 0; c < NA; ++c) dj[c] += a.az2 * q[c];
         }
@@ -264,43 +291,12 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
       for (int c = 0; c < NA; ++c) {
         double o = (double)eo[c], nn = (double)en[c];
         acc += o * o + nn * nn;
-        if (i < 2) eb[i][c] = 0.5 * (o + nn) / a.a[i];
+        // S_L = sum_a (Ebar_x B_y - Ebar_y B_x), Ebar the time mean of E / a
+        if (i == 0) s_l += 0.5 * (o + nn) / a.a[0] * (2.0 * (double)pry[c] / (a.a[0] * a.a[2]));
+        if (i == 1) s_l -= 0.5 * (o + nn) / a.a[1] * (-2.0 * (double)prx[c] / (a.a[1] * a.a[2]));
       }
       e2[i] = 0.5 * acc / (a.a[i] * a.a[i]);
     }
-    // magnetic terms from the plaquettes at the base site, with the link
-    // products in the state's representation:
-    // b_ij = ||U_i(x) U_j(x+i) - U_j(x) U_i(x+j)||_F^2 / (a_i a_j)^2
-    // (= 2 (N - Re tr U_ij) for unitary links, without its cancellation),
-    // B from Im tr t^a U_ij with U_ij = A B^dagger
-    typedef LinkIO<NC, R> IO;
-    double bxy, bxz = 0, byz = 0;
-    double Bx[NA], By[NA];
-    {
-      const M A = G::mul(Uo[0], IO::template load<R>(a.U, 1, a.g.V, n.p[0]));
-      const M B = G::mul(Uo[1], IO::template load<R>(a.U, 0, a.g.V, n.p[1]));
-      bxy = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[1] * a.a[0] * a.a[1]);
-    }
-#pragma unroll
-    for (int c = 0; c < NA; ++c) Bx[c] = By[c] = 0.0;
-    if (iz <= a.g.nz - 2) {
-      R pr[NA];
-      M A = G::mul(Uo[0], IO::template load<R>(a.U, 2, a.g.V, n.p[0]));  // U_x U_z(x+x)
-      M B = G::mul(Uo[2], IO::template load<R>(a.U, 0, a.g.V, n.p[2]));  // U_z U_x(x+z)
-      bxz = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[2] * a.a[0] * a.a[2]);
-      Group<NC, R>::proj(G::mul_d(A, B), pr);  // B_y = -2 Im tr t U_zx / (a_z a_x) = +2 Im tr t U_xz / (a_x a_z)
-#pragma unroll
-      for (int c = 0; c < NA; ++c) By[c] = 2.0 * (double)pr[c] / (a.a[0] * a.a[2]);
-      A = G::mul(Uo[1], IO::template load<R>(a.U, 2, a.g.V, n.p[1]));  // U_y U_z(x+y)
-      B = G::mul(Uo[2], IO::template load<R>(a.U, 1, a.g.V, n.p[2]));  // U_z U_y(x+z)
-      byz = Fro2<NC, R>::diff(A, B) / (a.a[1] * a.a[2] * a.a[1] * a.a[2]);
-      Group<NC, R>::proj(G::mul_d(A, B), pr);  // B_x = -2 Im tr t U_yz / (a_y a_z)
-#pragma unroll
-      for (int c = 0; c < NA; ++c) Bx[c] = -2.0 * (double)pr[c] / (a.a[1] * a.a[2]);
-    }
-    double s_l = 0;
-#pragma unroll
-    for (int c = 0; c < NA; ++c) s_l += eb[0][c] * By[c] - eb[1][c] * Bx[c];
     double e = 0.5 * (e2[0] + e2[1] + e2[2]) + bxy + bxz + byz;
     double p_t = 0.5 * e2[2] + bxy;
     double p_l = 0.5 * (e2[0] + e2[1]) + bxz + byz - p_t;
@@ -314,13 +310,24 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
   const int op[5] = {0, 0, 0, 0, 0};
   block_reduce<5>(sh, v, op);
   if (threadIdx.x == 0) {
-    const double inv = 1.0 / (double)a.g.nxy;
-    a.tab[iz * 4 + 0] = v[0] * inv;
-    a.tab[iz * 4 + 1] = v[1] * inv;
-    a.tab[iz * 4 + 2] = v[2] * inv;
-    a.tab[iz * 4 + 3] = v[3] * inv;
-    if (v[4] != 0.0) a.tab[iz * 4 + 0] = __longlong_as_double(0x7ff8000000000000LL);  // NaN marks it
+    double* out = a.part + ((int64_t)iz * a.split + blockIdx.y) * 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[k] = v[k];
   }
+}
+
+// tab[iz] = (sum over the split blocks of slice iz, in block order) / nxy;
+// a slice that met a non-finite value gets a NaN energy density.
+__global__ void k_tmunu_fold(const double* part, int split, int nz, double inv, double* tab) {
+  const int iz = blockIdx.x * blockDim.x + threadIdx.x;
+  if (iz >= nz) return;
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int p = 0; p < split; ++p)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] += part[((int64_t)iz * split + p) * 5 + k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) tab[iz * 4 + k] = v[k] * inv;
+  if (v[4] != 0.0) tab[iz * 4 + 0] = __longlong_as_double(0x7ff8000000000000LL);  // NaN marks it
 }
 
 template <int NC, typename R>
@@ -343,9 +350,23 @@ static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
-  a.tab = dev_tab ? dev_tab : c->tab;
-  k_tmunu<NC, R><<<c->g.nz, kRedThreads, 0, c->stream>>>(a);
+  // about 8 blocks per SM in all, at most kTmunuSplit per slice
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t per_slice = (c->g.nxy + kRedThreads - 1) / kRedThreads;
+  int64_t split = (8 * (int64_t)sms + c->g.nz - 1) / c->g.nz;
+  if (split > kTmunuSplit) split = kTmunuSplit;
+  if (split > per_slice) split = per_slice;
+  if (split < 1) split = 1;
+  a.split = (int)split;
+  a.part = c->tpart;
+  double* tab = dev_tab ? dev_tab : c->tab;
+  k_tmunu<NC, R><<<dim3((unsigned)c->g.nz, (unsigned)split), kRedThreads, 0, c->stream>>>(a);
   int st = cuda_check(cudaGetLastError(), "k_tmunu launch");
+  if (st) return st;
+  k_tmunu_fold<<<(c->g.nz + 127) / 128, 128, 0, c->stream>>>(c->tpart, (int)split, c->g.nz, 1.0 / (double)c->g.nxy,
+                                                              tab);
+  st = cuda_check(cudaGetLastError(), "k_tmunu_fold launch");
   if (st || !host_tab) return st;
   st = cuda_check(cudaMemcpyAsync(host_tab, c->tab, sizeof(double) * 4 * c->g.nz, cudaMemcpyDeviceToHost,
                                   c->stream),

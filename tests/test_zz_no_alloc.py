@@ -62,9 +62,11 @@ def _device_layout(G, h, dtype):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_static_residual_matches_context_residual(G, precision):
+@pytest.mark.parametrize("nc,nx,ny", [(3, 12, 10), (3, 7, 5), (2, 7, 5)])
+def test_static_residual_matches_context_residual(G, precision, nc, nx, ny):
+    """(3, 7, 5): the SU(3) link array ends in a padded block of 32 sites."""
     import torch
-    cfg = dict(gi.small_config(3), precision=precision)
+    cfg = dict(gi.small_config(nc, nx=nx, ny=ny), precision=precision)
     h = G.glasma_init_mv(cfg, None)
     dtype = torch.float64 if precision == "fp64" else torch.float32
     p = h.params
