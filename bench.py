@@ -92,10 +92,10 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def load_traffic(workload, precision, nz):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu
-    summary, valid only for the workload's own lattice and if the kernel
-    sources are unchanged since."""
+def load_profile_entry(workload, precision, nz):
+    """The committed ncu figures of the step kernel (per-launch DRAM bytes
+    and FFMA count), valid only for the workload's own lattice and if the
+    kernel sources are unchanged since; else None."""
     path = os.path.join(ROOT, "profiles", "step_traffic.json")
     try:
         if nz != gi.CONFIGS[workload]["nz"]:
@@ -103,10 +103,20 @@ def load_traffic(workload, precision, nz):
         d = json.load(open(path))
         e = d[workload + ":" + precision]
         if e["kernel_hash"] == step_kernel_hash():
-            return e["dram_bytes_per_launch"]
+            return e
     except Exception:
         pass
     return None
+
+
+def load_traffic(workload, precision, nz):
+    e = load_profile_entry(workload, precision, nz)
+    return e["dram_bytes_per_launch"] if e else None
+
+
+# FP32 FMA lanes per SM and SMs of a GB300: the ALU peak is lanes x SMs x
+# the maximum SM clock
+FP32_LANES_PER_SM, GB300_SMS = 128, 152
 
 
 # ---------------------------------------------------------------------------
@@ -323,11 +333,22 @@ def run_ours(args, cfg):
     alg = V * bytes_per_site(nc, rs) + (hops / K) * qbytes
     peak, peak_kind = load_peaks()
     achieved = alg / (per_launch_ms * 1e-3) / 1e9
-    traffic = load_traffic(args.workload, args.precision, cfg["nz"])
+    prof = load_profile_entry(args.workload, args.precision, cfg["nz"])
+    traffic = prof["dram_bytes_per_launch"] if prof else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "kernel": "k_step_leapfrog", "peak_source": peak_kind,
             "alg_bytes_per_launch": alg}
+    if prof and prof.get("ffma_per_launch"):
+        # the FP32 FMA pipe next to HBM: the kernel's FFMA count (ncu) over
+        # its live launch time, against lanes x SMs x the maximum SM clock
+        mhz = clk.summary().get("sm_max_mhz") or 2070.0
+        peak_fma = FP32_LANES_PER_SM * GB300_SMS * mhz * 1e6 / 1e12
+        got_fma = prof["ffma_per_launch"] / (per_launch_ms * 1e-3) / 1e12
+        roof["fma_pipe"] = {"achieved": got_fma, "peak": peak_fma, "unit": "TFMA/s",
+                            "frac": got_fma / peak_fma,
+                            "ffma_per_launch": prof["ffma_per_launch"],
+                            "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
 
     extras = {}
     if rank == 0 and not args.no_extras:
