@@ -159,13 +159,10 @@ template <> struct ImplOcc<double> { static constexpr int blocks = 1; };
 // force of the two fixed time slots.  The first iterate is written before
 // the staples, so U_n(x) and E(t_{n-1/2}) are not live across them.
 template <int NC, typename R>
-__global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_prep(ImplArgs<R> a) {
+__device__ __forceinline__ void prep_link(const ImplArgs<R>& a, int i, uint32_t t, int iz) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  const int i = (int)threadIdx.y;
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int iz = (int)blockIdx.y;
   if (t >= (uint32_t)a.g.nxy) return;
   if (i == 2 && iz == a.g.nz - 1) return;
   const int64_t s = (int64_t)iz * a.g.nxy + t;
@@ -216,6 +213,21 @@ __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_prep(ImplA
   for (int c = 0; c < NA; ++c) a.Ework[(int64_t)(i * NA + c) * a.g.V + s] = ew[c] + a.dt * F[c];
 }
 
+// Slices per block of the prepare and sweep kernels.  A block marches
+// through kImplZ consecutive z slices of its transverse tile, so the links
+// of slice z+1 that it reads as neighbours are in L1 when they become its
+// own links (the sweep reads two link arrays in the planes containing z):
+// 87 -> 70 ms per step of the SU(3) 2048 x 128^2 workload.
+constexpr int kImplZ = 16;
+
+template <int NC, typename R>
+__global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_prep(ImplArgs<R> a) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int z0 = (int)blockIdx.y * kImplZ;
+#pragma unroll 1
+  for (int k = 0; k < kImplZ && z0 + k < a.g.nz; ++k) prep_link<NC, R>(a, (int)threadIdx.y, t, z0 + k);
+}
+
 // One fixed-point sweep: E = Ework + dt F_0(X), Xn = exp(i dt E) U_n, where
 // Ework already holds E(t_{n-1/2}) + dt J + dt (F_1(U_n) + F_2(U_{n-1})).
 template <int NC, typename R>
@@ -231,10 +243,12 @@ __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplA
   __shared__ R smax[6], semax[6];
   const int i = (int)threadIdx.y;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int iz = (int)blockIdx.y;
   R dmax = R(0), emax = R(0);
-  const bool live = t < (uint32_t)a.g.nxy && !(i == 2 && iz == a.g.nz - 1);
-  if (live) {
+  const int z0 = (int)blockIdx.y * kImplZ;
+#pragma unroll 1
+  for (int kz = 0; kz < kImplZ && z0 + kz < a.g.nz; ++kz) {
+    const int iz = z0 + kz;
+    if (t >= (uint32_t)a.g.nxy || (i == 2 && iz == a.g.nz - 1)) continue;
     const SiteNbr n = site_nbr_tz(a.g, t, iz);
     const int64_t s = n.s;
     R F[NA];
@@ -307,6 +321,7 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   // blocks per z slice (the directions share neighbour links in L1)
   const dim3 bs(64, 3);
   const dim3 grid((unsigned)((c->g.nxy + 63) / 64), (unsigned)c->g.nz);
+  const dim3 gridz(grid.x, (unsigned)((c->g.nz + kImplZ - 1) / kImplZ));
   int st;
   if (!c->uprev_valid) {
     a.Uout = (V2*)prev;
@@ -320,14 +335,14 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   st = cuda_check(cudaMemsetAsync(c->conv, 0, sizeof(double) * 2 * (maxit + 1), c->stream), "conv clear");
   if (st) return st;
   a.Xn = (V2*)xa;
-  k_implicit_prep<NC, R><<<grid, bs, 0, c->stream>>>(a);
+  k_implicit_prep<NC, R><<<gridz, bs, 0, c->stream>>>(a);
   st = cuda_check(cudaGetLastError(), "k_implicit_prep launch");
   if (st) return st;
   for (int k = 0; k < maxit; ++k) {
     a.k = k;
     a.X = (const V2*)(k % 2 == 0 ? xa : xb);
     a.Xn = (V2*)(k % 2 == 0 ? xb : xa);
-    k_implicit_iter<NC, R><<<grid, bs, 0, c->stream>>>(a);
+    k_implicit_iter<NC, R><<<gridz, bs, 0, c->stream>>>(a);
     st = cuda_check(cudaGetLastError(), "k_implicit_iter launch");
     if (st) return st;
   }
