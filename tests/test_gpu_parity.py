@@ -287,6 +287,29 @@ def test_implicit_fp32_matches_oracle(G, nc):
     assert np.max(np.abs(tab[:, 0] - rtab[:, 0])) / np.max(rtab[:, 0]) < 1e-4
 
 
+@pytest.mark.parametrize("nc", [2, 3])
+def test_implicit_fp32_stops_at_its_rounding_level(G, nc):
+    """FP32 semi-implicit steps with the default tolerance (1e-14, out of
+    FP32's reach): the iteration must stop on its rounding-level rules
+    (contraction bound or stagnation) within a few sweeps, and agree with
+    the FP64 oracle iterated to 1e-14 as closely as the tolerance-stopped
+    FP32 run does."""
+    cfg = gi.small_config(nc, nz=64, nx=7, ny=6, a_z=0.5, dt=0.25,
+                          sigma_l=1.5, steps=10)
+    cfg.update(scheme="implicit", implicit_max_iter=60, precision="fp32")
+    p = O.Params.from_dict(cfg)
+    rho = gi.mv_rho(cfg["seed"], nc, p.nx, p.ny, p.g2mu)
+    h = G.glasma_init_mv(cfg, rho)
+    iters = []
+    for _ in range(cfg["steps"]):
+        G.glasma_step(h, 1)
+        iters.append(G.glasma_get_info(h).implicit_iters)
+    assert max(iters) <= 12, iters
+    st = O.step_implicit(O.init_mv(p, rho), cfg["steps"], tol=1e-14)
+    U, E, QA, QB, n = G.glasma_get_fields(h)
+    assert rel(U, st.U) < 3e-5 and rel(E, st.E) < 3e-5
+
+
 def test_implicit_not_converged_is_reported(G):
     cfg = gi.small_config(2, nz=64, nx=7, ny=6, a_z=0.5, dt=0.25,
                           sigma_l=1.5, steps=3)
