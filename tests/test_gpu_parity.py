@@ -310,6 +310,28 @@ def test_implicit_fp32_stops_at_its_rounding_level(G, nc):
     assert rel(U, st.U) < 3e-5 and rel(E, st.E) < 3e-5
 
 
+def test_improved_workload_full_size_properties(G):
+    """The benchmarked improved-scheme configuration at full size (SU(3)
+    2048 x 128^2, a_z = dt = a_T/4, FP32, the launch configuration of
+    bench.py): properties that hold at any size, since the oracle cannot
+    hold this lattice.  Every step converges within a few sweeps, the field
+    energy is conserved to FP32 rounding over the steps (the nuclei are
+    still apart) and the Gauss residual stays small against the charge."""
+    cfg = dict(gi.CONFIGS["su3_2048x128x128_improved"])
+    h = G.glasma_init_mv(cfg, None)
+    _, H0 = G.glasma_tmunu(h)
+    iters = []
+    for _ in range(6):
+        G.glasma_step(h, 1)
+        iters.append(G.glasma_get_info(h).implicit_iters)
+    _, H1 = G.glasma_tmunu(h)
+    gmax, grms, rmax = G.glasma_gauss_residual(h)
+    G.glasma_free(h)
+    assert all(2 <= k <= 12 for k in iters), iters
+    assert abs(H1 / H0 - 1.0) < 1e-5, (H0, H1)
+    assert gmax < 1e-3 * rmax, (gmax, rmax)
+
+
 def test_implicit_not_converged_is_reported(G):
     cfg = gi.small_config(2, nz=64, nx=7, ny=6, a_z=0.5, dt=0.25,
                           sigma_l=1.5, steps=3)
