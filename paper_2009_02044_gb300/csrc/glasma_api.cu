@@ -356,7 +356,8 @@ static int dl(glasma_ctx* c, std::vector<T>& h, const void* d, size_t count) {
 
 extern "C" {
 
-// device link array (storage precision) -> host doubles [3][V][NV][2]
+// device link array (storage precision) -> host doubles, element for element
+// in the device order (see link_index)
 static int links_to_host(glasma_ctx* c, const void* dev, std::vector<double>& out) {
   const size_t n = 2 * (size_t)link_elems(c->p.nc, c->g.V);
   out.resize(n);

@@ -33,10 +33,10 @@ namespace glasma {
 // sweep cannot improve the iterate), with the rate c taken as the larger
 // of the last two observed ratios d_k / d_(k-1) and d_(k-1) / d_(k-2)
 // (the first sweeps remove fast modes and contract faster than the last
-// ones) and required below 1/2; or if
-// d_k no longer decreases while already within 1024 unit roundoffs of
-// max|E| (the rounding floor).  A change that stops decreasing above that
-// floor is a failing iteration (e.g. dt^2 K_T / 4 > 1), not convergence.
+// ones) and required below 1/2; or if d_k no longer decreases while
+// already within 1024 unit roundoffs of max|E| (the rounding floor).  A
+// change that stops decreasing above that floor is a failing iteration
+// (e.g. dt^2 K_T / 4 > 1), not convergence.
 GL_HD bool implicit_converged(const double* conv, int maxit, int k, double tol, bool fp32) {
   const double d = conv[k];
   if (d < tol) return true;
