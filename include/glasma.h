@@ -80,7 +80,7 @@ typedef struct {
                                iteration also ends when the contraction
                                bound d c / (1 - c) (d = max |dE|, c the
                                larger of the last two ratios of d, below
-                               1/2) is at most 8 unit roundoffs of max |E|,
+                               1/2) is at most 16 unit roundoffs of max |E|,
                                or when max |dE| stops decreasing within
                                1024 unit roundoffs of max |E| (the
                                precision's rounding floor) */

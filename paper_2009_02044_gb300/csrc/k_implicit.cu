@@ -28,15 +28,15 @@ namespace glasma {
 
 // Iteration k has converged if its largest change d_k = max|dE| is below
 // the tolerance; or if the error bound of a contraction, d_k c / (1 - c),
-// is at most 8 unit roundoffs of max|E| (below the noise of one sweep's
-// rounding, about 10 to 20 unit roundoffs of max|E| in FP32, so one more
-// sweep cannot improve the iterate), with the rate c taken as the larger
-// of the last two observed ratios d_k / d_(k-1) and d_(k-1) / d_(k-2)
-// (the first sweeps remove fast modes and contract faster than the last
-// ones) and required below 1/2; or if d_k no longer decreases while
-// already within 1024 unit roundoffs of max|E| (the rounding floor).  A
-// change that stops decreasing above that floor is a failing iteration
-// (e.g. dt^2 K_T / 4 > 1), not convergence.
+// is at most 16 unit roundoffs of max|E| (the noise that one sweep's
+// rounding leaves, 10 to 50 unit roundoffs of max|E| in FP32 depending on
+// the fields, so one more sweep cannot improve the iterate), with the rate
+// c taken as the larger of the last two observed ratios d_k / d_(k-1) and
+// d_(k-1) / d_(k-2) (the first sweeps remove fast modes and contract
+// faster than the last ones) and required below 1/2; or if d_k no longer
+// decreases while already within 1024 unit roundoffs of max|E| (the
+// rounding floor).  A change that stops decreasing above that floor is a
+// failing iteration (e.g. dt^2 K_T / 4 > 1), not convergence.
 GL_HD bool implicit_converged(const double* conv, int maxit, int k, double tol, bool fp32) {
   const double d = conv[k];
   if (d < tol) return true;
@@ -45,7 +45,7 @@ GL_HD bool implicit_converged(const double* conv, int maxit, int k, double tol, 
   const double emax = conv[maxit + 1 + k];
   if (k >= 2 && conv[k - 1] > 0.0 && conv[k - 2] > 0.0) {
     const double c = fmax(d / conv[k - 1], conv[k - 1] / conv[k - 2]);
-    if (c < 0.5 && d * c <= 8.0 * u * emax * (1.0 - c)) return true;
+    if (c < 0.5 && d * c <= 16.0 * u * emax * (1.0 - c)) return true;
   }
   if (d < conv[k - 1]) return false;
   return d <= 1024.0 * u * emax;
