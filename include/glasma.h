@@ -319,6 +319,22 @@ GLASMA_API int glasma_fit_gaussian(const double* x, const double* f, int n, doub
                                    double* sigma);
 
 /*
+ * The stopping rule of the improved scheme's fixed-point iteration, as the
+ * library applies it after every sweep (host computation, no GPU):
+ * dmax[j] = max |E^(j+1) - E^(j)| and emax[j] = max |E^(j+1)| of sweeps
+ * j = 0..k; *converged = 1 if the iteration stops after sweep k, else 0.
+ * It stops when dmax[k] < tol; or when the contraction bound
+ * dmax[k] c / (1 - c) is at most 16 unit roundoffs of emax[k], with c the
+ * larger of dmax[k] / dmax[k-1] and dmax[k-1] / dmax[k-2] (k >= 2) and
+ * c < 1/2; or when dmax[k] >= dmax[k-1] while dmax[k] is within 1024 unit
+ * roundoffs of emax[k] (the precision's rounding floor).  precision:
+ * GLASMA_FP32 or GLASMA_FP64 (the state's, which sets the unit roundoff).
+ * Errors: INVALID_ARG (NULL pointers, k outside 0..4096, bad precision).
+ */
+GLASMA_API int glasma_implicit_converged(const double* dmax, const double* emax, int k, double tol, int precision,
+                                         int* converged);
+
+/*
  * Gradient of the mid-rapidity energy with respect to the initial MV colour
  * charges (SU(2), leapfrog, one colour sheet): the hand-written adjoint of
  * glasma_init_mv followed by n_steps glasma_step calls.  The observable is

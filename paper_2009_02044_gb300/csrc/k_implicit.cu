@@ -376,6 +376,24 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   return GLASMA_OK;
 }
 
+}  // namespace glasma
+
+extern "C" int glasma_implicit_converged(const double* dmax, const double* emax, int k, double tol, int precision,
+                                         int* converged) {
+  if (!dmax || !emax || !converged || k < 0 || k > 4096 ||
+      (precision != GLASMA_FP32 && precision != GLASMA_FP64))
+    return glasma::set_error(GLASMA_ERR_INVALID_ARG, "glasma_implicit_converged: bad arguments");
+  std::vector<double> conv(2 * ((size_t)k + 1), 0.0);
+  for (int j = 0; j <= k; ++j) {
+    conv[j] = dmax[j];
+    conv[k + 1 + j] = emax[j];
+  }
+  *converged = glasma::implicit_converged(conv.data(), k, k, tol, precision == GLASMA_FP32) ? 1 : 0;
+  return GLASMA_OK;
+}
+
+namespace glasma {
+
 int launch_step_implicit(glasma_ctx* c, bool hop, int* iters) {
   if (c->p.nc == 2) return c->rs == 8 ? implicit_t<2, double>(c, hop, iters) : implicit_t<2, float>(c, hop, iters);
   return c->rs == 8 ? implicit_t<3, double>(c, hop, iters) : implicit_t<3, float>(c, hop, iters);

@@ -102,6 +102,8 @@ def load_library(path=LIB_PATH):
                                          C.c_double, C.c_double, C.c_double,
                                          C.c_double, P, P, C.c_longlong,
                                          C.c_int, P, P]),
+        "glasma_implicit_converged": (C.c_int, [dp, dp, C.c_int, C.c_double, C.c_int,
+                                                 C.POINTER(C.c_int)]),
         "glasma_fit_gaussian": (C.c_int, [dp, dp, C.c_int, C.c_double, dp, dp,
                                           dp]),
         "glasma_adjoint_energy": (C.c_int, [C.POINTER(glasma_params), dp,
@@ -453,6 +455,21 @@ def glasma_sample_grid(grid, n_t, nz, stride, comp, t0, dts, z0, az, x, y,
         float(t0), float(dts), float(z0), float(az), C.c_void_p(x),
         C.c_void_p(y), int(n_pts), {"milne": 0, "lab": 1}[coords],
         C.c_void_p(out), _stream_ptr(stream)), "glasma_sample_grid")
+
+
+def glasma_implicit_converged(dmax, emax, tol=1e-14, precision="fp32"):
+    """Whether the improved scheme's iteration stops after the last of the
+    sweeps whose max |dE| and max |E| are given (host computation)."""
+    d = np.ascontiguousarray(dmax, dtype=np.float64)
+    e = np.ascontiguousarray(emax, dtype=np.float64)
+    if d.size == 0 or d.size != e.size:
+        raise ValueError("dmax and emax need the same, non-zero length")
+    out = C.c_int()
+    prec = FP32 if precision in ("fp32", FP32) else FP64
+    _check(load_library().glasma_implicit_converged(
+        _dptr(d), _dptr(e), d.size - 1, float(tol), prec, C.byref(out)),
+        "glasma_implicit_converged")
+    return bool(out.value)
 
 
 def glasma_fit_gaussian(x, f, frac=0.1):

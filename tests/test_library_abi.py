@@ -102,3 +102,35 @@ def test_host_gaussian_fit_matches_oracle(lib):
         G.glasma_fit_gaussian(eta, np.exp(eta ** 2 / 8), 0.0)
     with pytest.raises(G.GlasmaError):
         G.glasma_fit_gaussian(eta[:2], f[:2], 0.0)
+
+
+def test_implicit_stopping_rule_on_measured_sequences(lib):
+    """The improved scheme's stopping rule (host code) on the sequences of
+    max |dE| measured on the SU(3) 2048 x 128^2 FP32 run, in units of
+    u max|E| (u = 2^-24): it stops at the first sweep whose contraction
+    bound is below the sweep's rounding noise, not on a first ratio that
+    only reflects fast modes, and not while the change stagnates above the
+    rounding floor."""
+    from paper_2009_02044_gb300 import glasma as G
+    u = 2.0 ** -24
+    emax = 0.0123
+
+    def stops(seq, **kw):
+        d = np.asarray(seq, dtype=float) * u * emax
+        return [G.glasma_implicit_converged(d[:k + 1], np.full(k + 1, emax), **kw)
+                for k in range(len(seq))]
+
+    # before the collision: the bound after the third sweep, 120 * 0.064 /
+    # 0.936 = 8.2, is already below 16 (the next change measured 10)
+    assert stops([1.28e6, 1.87e3, 120, 10]) == [False, False, True, True]
+    # after it: the floor is higher and the ratios creep up near it
+    assert stops([4.52e6, 2.74e5, 2.1e4, 1.82e3, 181, 41]) == [False] * 5 + [True]
+    # a change that stops decreasing at the floor is convergence ...
+    assert stops([1e6, 1e3, 300, 200, 210]) == [False] * 4 + [True]
+    # ... above it, a failing iteration (contraction near or above 1)
+    assert not any(stops([1e6, 6e5, 5e5, 5e5, 5.1e5]))
+    # the tolerance alone, at any sweep
+    assert stops([1.0, 0.5], tol=1.0 * u * emax * 2) == [True, True]
+    # FP64 units: the same sequence in FP32 units is far above FP64's floor
+    assert not any(stops([1.28e6, 1.87e3, 120, 10], precision="fp64"))
+    assert lib.glasma_implicit_converged(None, None, 0, 0.0, 1, None) == -1
