@@ -14,6 +14,28 @@ exchange); value = all ranks' site-updates / max-over-ranks time.
 The reference arm (--impl reference) times the FP64 CPU oracle, as it
 stands, on the host cores: each step is one oracle step of a two-slice
 64 x 64 slab of the same SU(3) workload (a bounded sample).
+
+Fields of the JSON line beyond the metric:
+  roofline      the step kernel (the only kernel of the timed region):
+                achieved = compulsory bytes per launch (read and write 3
+                links and 3 fields per site, plus the charge windows on hop
+                steps) / its launch time from CUDA events, against the
+                measured HBM copy bandwidth; traffic = DRAM bytes per launch
+                from the committed ncu capture (null once the kernel sources
+                differ from the captured ones); fma_pipe = the FFMA count of
+                the same capture over the launch time, against 152 SMs x 128
+                FP32 lanes x the maximum SM clock
+  e2e           the same metric through the C ABI from host charges: the
+                initial state, the K steps and T^{mu nu} to the host, wall
+                clock, with the bytes copied each way per step
+  cpu_baseline  the FP64 oracle on a bounded slab of the workload, with the
+                cores it used
+  clocks        SM clocks and throttle reasons sampled during the timed
+                region
+  extras        (unless --no-extras) the FP64 path and the FP32 energy-
+                density error against it, one T^{mu nu} sample, the improved
+                scheme on its 2048 x 128^2 workload, the batched ensemble,
+                the rest-frame analysis and the adjoint gradient
 """
 from __future__ import annotations
 
