@@ -81,9 +81,12 @@ typedef struct {
                                bound d c / (1 - c) (d = max |dE|, c the
                                larger of the last two ratios of d, below
                                1/2) is at most 16 unit roundoffs of max |E|,
-                               or when max |dE| stops decreasing within
+                               or when max |dE| is within 64 unit
+                               roundoffs of max |E| and falls by less than
+                               half, or when it stops decreasing within
                                1024 unit roundoffs of max |E| (the
-                               precision's rounding floor) */
+                               precision's rounding floor); see
+                               glasma_implicit_converged */
   int n_sheets;             /* longitudinal colour sheets per nucleus
                                (0 or 1: the single-sheet MV charge; S > 1,
                                at most 64: S independent transverse charges,
@@ -326,8 +329,9 @@ GLASMA_API int glasma_fit_gaussian(const double* x, const double* f, int n, doub
  * It stops when dmax[k] < tol; or when the contraction bound
  * dmax[k] c / (1 - c) is at most 16 unit roundoffs of emax[k], with c the
  * larger of dmax[k] / dmax[k-1] and dmax[k-1] / dmax[k-2] (k >= 2) and
- * c < 1/2; or when dmax[k] >= dmax[k-1] while dmax[k] is within 1024 unit
- * roundoffs of emax[k] (the precision's rounding floor).  precision:
+ * c < 1/2; or when dmax[k] is within 64 unit roundoffs of emax[k] and at
+ * least dmax[k-1] / 2; or when dmax[k] >= dmax[k-1] while dmax[k] is within
+ * 1024 unit roundoffs of emax[k] (the precision's rounding floor).  precision:
  * GLASMA_FP32 or GLASMA_FP64 (the state's, which sets the unit roundoff).
  * Errors: INVALID_ARG (NULL pointers, k outside 0..4096, bad precision).
  */

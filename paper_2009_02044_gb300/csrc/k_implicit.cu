@@ -33,7 +33,9 @@ namespace glasma {
 // the fields, so one more sweep cannot improve the iterate), with the rate
 // c taken as the larger of the last two observed ratios d_k / d_(k-1) and
 // d_(k-1) / d_(k-2) (the first sweeps remove fast modes and contract
-// faster than the last ones) and required below 1/2; or if d_k no longer
+// faster than the last ones) and required below 1/2; or if d_k is within
+// 64 unit roundoffs of max|E| and no longer falls by half per sweep (the
+// changes are then the rounding noise itself); or if d_k no longer
 // decreases while already within 1024 unit roundoffs of max|E| (the
 // rounding floor).  A change that stops decreasing above that floor is a
 // failing iteration (e.g. dt^2 K_T / 4 > 1), not convergence.
@@ -47,6 +49,7 @@ GL_HD bool implicit_converged(const double* conv, int maxit, int k, double tol, 
     const double c = fmax(d / conv[k - 1], conv[k - 1] / conv[k - 2]);
     if (c < 0.5 && d * c <= 16.0 * u * emax * (1.0 - c)) return true;
   }
+  if (d <= 64.0 * u * emax && d >= 0.5 * conv[k - 1]) return true;
   if (d < conv[k - 1]) return false;
   return d <= 1024.0 * u * emax;
 }

@@ -125,6 +125,8 @@ def test_implicit_stopping_rule_on_measured_sequences(lib):
     assert stops([1.28e6, 1.87e3, 120, 10]) == [False, False, True, True]
     # after it: the floor is higher and the ratios creep up near it
     assert stops([4.52e6, 2.74e5, 2.1e4, 1.82e3, 181, 41]) == [False] * 5 + [True]
+    # changes within 64 ulps that no longer halve are the rounding noise
+    assert stops([1e6, 1e5, 1e4, 2000, 300, 100, 60]) == [False] * 6 + [True]
     # a change that stops decreasing at the floor is convergence ...
     assert stops([1e6, 1e3, 300, 200, 210]) == [False] * 4 + [True]
     # ... above it, a failing iteration (contraction near or above 1)
