@@ -13,12 +13,13 @@
 // Buffers: Uprev = U(t_{n-1}), U[cur] = U(t_n), the other U buffer and Uit
 // hold the iterates of U(t_{n+1}); E is iterated in place, Ework keeps
 // E(t_{n-1/2}) + dt J + dt times the force of the two fixed slots (t_n and
-// t_{n-1}), which the prepare kernel evaluates once per step.  conv[k] is the largest |E^(k+1) - E^(k)| of
-// iteration k (atomicMax on the bit pattern of a non-negative double).
-// The iteration ends when that change is below implicit_tol or stops
-// decreasing at the rounding floor of the state's precision (reached first in
-// FP32; see implicit_converged).  Iteration k returns at once once either
-// holds; if neither holds within implicit_max_iter the step reports
+// t_{n-1}), which the prepare kernel evaluates once per step.  conv[k] is
+// the largest |E^(k+1) - E^(k)| of iteration k and conv[maxit + 1 + k] the
+// largest |E^(k+1)| (atomicMax on the bit pattern of a non-negative
+// double).  The iteration ends when implicit_converged holds: the change is
+// below implicit_tol, or it has reached the rounding level of the state's
+// precision (always first in FP32).  Every launch after that returns at
+// once; if it never holds within implicit_max_iter the step reports
 // NOT_CONVERGED.
 #include <vector>
 
