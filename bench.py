@@ -485,11 +485,45 @@ def run_extras(G, torch, cfg, args, stream, value):
         "max_rel": err, "definition":
             "max over z and sampled t (every 50 steps) of |eps32 - eps64| / "
             "max eps64; FP64 path parity-checked against the oracle"}
+    out["su2_fp32"] = run_su2(G, torch, stream)
     out["improved"] = run_improved(G, torch, stream)
     out["ensemble"] = run_ensemble(G, torch, stream)
     out["observables"] = run_observables(G, torch, stream)
     out["adjoint"] = run_adjoint(G, torch)
     return out
+
+
+def run_su2(G, torch, stream, steps=100, warm=5):
+    """The same leapfrog kernel for SU(2) in FP32 on a 1024 x 128^2 event
+    (2.8 GB of state per step): 168 compulsory bytes per site, a quarter of
+    SU(3)'s, with far less arithmetic, reported next to the SU(3) figure to
+    show the kernel where its arithmetic per byte is low."""
+    cfg = dict(gi.CONFIGS["su2_1024x128x128"])
+    V = cfg["nz"] * cfg["nx"] * cfg["ny"]
+    with torch.cuda.stream(stream):
+        h = G.glasma_init_mv(cfg, None, stream=stream)
+    G.glasma_step(h, warm)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    G.glasma_step(h, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = G.glasma_get_info(h).kernel_launches
+    G.glasma_free(h)
+    per_launch = ms / launches
+    alg = V * bytes_per_site(2, 4)
+    peak, kind = load_peaks()
+    gbs = alg / (per_launch * 1e-3) / 1e9
+    return {"workload": "su2_1024x128x128", "value": V * steps / (ms * 1e-3),
+            "unit": METRIC, "ms_per_step": ms / steps, "steps_timed": steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak,
+                         "unit": "GB/s", "frac": gbs / peak, "peak_source": kind,
+                         "alg_bytes_per_launch": alg,
+                         "note": "compulsory bytes only (the charge windows of "
+                                 "hop steps are left out)"}}
 
 
 def run_adjoint(G, torch, probes=4, h=1e-4):

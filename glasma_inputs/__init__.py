@@ -50,6 +50,11 @@ CONFIGS = {
     "su2_256x32x32": _cfg(nc=2, nz=256, nx=32, ny=32, a_z=1.0, dt=0.5,
                           sigma_l=4.0, g2mu=0.1, m_ir=0.2, seed=1004,
                           steps=200, precision="fp32"),
+    # SU(2) 1024 x 128^2, FP32: the leapfrog kernel where its arithmetic
+    # per byte is low (168 B per site)
+    "su2_1024x128x128": _cfg(nc=2, nz=1024, nx=128, ny=128, a_z=1.0, dt=0.5,
+                             sigma_l=8.0, g2mu=0.1, m_ir=0.2, seed=1006,
+                             steps=200, precision="fp32"),
     # SU(3) 2048 x 128^2 thin nuclei, improved scheme, a_z = dt = 0.25
     "su3_2048x128x128_improved": _cfg(nc=3, nz=2048, nx=128, ny=128,
                                       a_z=0.25, dt=0.25, sigma_l=2.0,
