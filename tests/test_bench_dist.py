@@ -49,3 +49,29 @@ def test_single_rank_aggregate():
     import bench
     ms, v = bench.aggregate(10.0, 100, 10, 1)
     assert ms == 10.0 and v == pytest.approx(100 * 10 / 0.010)
+
+
+def test_compulsory_bytes_per_site():
+    """The roofline's algorithmic bytes: read and write 3 links and 3 E
+    fields once per site (SU(2): 4 reals per link, SU(3): 18; fields
+    nc^2 - 1 reals)."""
+    import bench
+    assert bench.bytes_per_site(3, 4) == 624
+    assert bench.bytes_per_site(3, 8) == 1248
+    assert bench.bytes_per_site(2, 8) == 336
+    assert bench.bytes_per_site(2, 4) == 168
+
+
+def test_profile_figures_are_tied_to_the_kernel_sources(monkeypatch):
+    """The committed ncu figures (DRAM bytes, FFMA count) are used only for
+    the captured workload and only while the step kernel's sources hash to
+    the captured value; otherwise the bench reports them as null."""
+    import bench
+    e = bench.load_profile_entry("su3_512x64x64", "fp32", 512)
+    if e is not None:
+        assert e["dram_bytes_per_launch"] > 0 and e.get("ffma_per_launch", 1) > 0
+    assert bench.load_profile_entry("su3_512x64x64", "fp32", 160) is None
+    assert bench.load_profile_entry("su3_512x64x64", "fp64", 512) is None
+    monkeypatch.setattr(bench, "step_kernel_hash", lambda: "0" * 16)
+    assert bench.load_profile_entry("su3_512x64x64", "fp32", 512) is None
+    assert bench.load_traffic("su3_512x64x64", "fp32", 512) is None
