@@ -454,9 +454,11 @@ def run_extras(G, torch, cfg, args, stream, value):
                            "what": "one T^{mu nu}(z) sample of the state (k_tmunu, "
                                    "FP64 sums, device output), timed apart from the steps"}
     G.glasma_free(hs)
-    # FP64 comparison run (same event) and energy-density error
+    # FP64 comparison run (same event) and energy-density error over the
+    # workload's full step count, whatever --steps is (outside the timed
+    # region)
     other = "fp64" if args.precision == "fp32" else "fp32"
-    k64 = min(K, 400)
+    k64 = int(p["steps"])
     res = {}
     for prec in (args.precision, other):
         c = dict(p, precision=prec)

@@ -209,14 +209,18 @@ GLASMA_API int glasma_tmunu_device(glasma_ctx* c, double* dev_out);
  * Outputs are host doubles (any may be NULL), as in glasma_gauss_residual.
  * Scratch: a fixed device array inside the library, one row of partials
  * per z slice, so nz may be at most 8192; larger nz is rejected with
- * GLASMA_ERR_INVALID_ARG before any GPU work.  Every GPU that loads the
- * library keeps that array (256 KB) until the process exits.  The first
- * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  All calls share
- * the one array, so calls that overlap on the GPU (other streams, other
- * threads) race and must be serialised by the caller.  Work runs on
- * `stream` (cudaStream_t, NULL = legacy default), which the call
- * synchronises.  Errors: INVALID_ARG, NONFINITE, CUDA.
+ * GLASMA_ERR_INVALID_ARG before any GPU work.  Each call looks up the
+ * array's device address with the current device (the one that holds the
+ * fields).  With CUDA's lazy module loading, the first call on a device
+ * loads this entry point's device code and its 256 KB array, which the GPU
+ * then keeps until the process exits: make that first call while device
+ * memory is still available (for example right after the context is
+ * created); later calls allocate nothing.  All calls share the one array,
+ * so calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  Work runs on `stream` (cudaStream_t,
+ * NULL = legacy default); the call synchronises it and copies the result
+ * to pageable host memory, so it cannot be recorded into a CUDA graph.
+ * Errors: INVALID_ARG, NONFINITE, CUDA.
  */
 GLASMA_API int glasma_gauss_residual_static(int nc, int precision, int nz, int ny, int nx, double a_t,
                                             double a_z, const void* U, const void* E, const void* QA,

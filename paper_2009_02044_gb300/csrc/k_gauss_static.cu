@@ -1,8 +1,6 @@
 // Gauss-law residual over caller-owned device fields that allocates no
 // device memory: its scratch is a fixed array in this file (see
 // glasma_gauss_residual_static in glasma.h).
-#include <mutex>
-
 #include "glasma_internal.cuh"
 
 namespace glasma {
@@ -114,24 +112,27 @@ __global__ void __launch_bounds__(kStaticThreads) k_gauss_static_fold(double* sc
     for (int k = 0; k < 4; ++k) scratch[kStaticMaxSlices * 4 + k] = v[k];
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (cudaGetSymbolAddress; the name itself is only a host-side
-// stand-in and must never be passed to a kernel).
+// Device address of the scratch array on the current device
+// (cudaGetSymbolAddress; the name itself is only a host-side stand-in and
+// must never be passed to a kernel).  It is looked up on every call, so a
+// module reloaded after a device reset is never addressed through a stale
+// pointer.  The same call makes sure every kernel of this file is loaded:
+// with lazy module loading the first call on a device is the one that loads
+// this code and its array, so no later call (of any N_c or precision) loads
+// anything.
 static int static_scratch(double** out) {
-  static std::mutex mu;
-  static double* addr[128] = {nullptr};
-  int dev = 0;
-  int st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  void* p = nullptr;
+  int st = cuda_check(cudaGetSymbolAddress(&p, g_gauss_scratch), "cudaGetSymbolAddress(g_gauss_scratch)");
   if (st) return st;
-  if (dev < 0 || dev >= 128) return set_error(GLASMA_ERR_INTERNAL, "device index out of range");
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    st = cuda_check(cudaGetSymbolAddress(&p, g_gauss_scratch), "cudaGetSymbolAddress(g_gauss_scratch)");
-    if (st) return st;
-    addr[dev] = (double*)p;
+  const void* fns[5] = {(const void*)k_gauss_static_slices<2, double>, (const void*)k_gauss_static_slices<2, float>,
+                        (const void*)k_gauss_static_slices<3, double>, (const void*)k_gauss_static_slices<3, float>,
+                        (const void*)k_gauss_static_fold};
+  for (int k = 0; k < 5 && !st; ++k) {
+    cudaFuncAttributes fa;
+    st = cuda_check(cudaFuncGetAttributes(&fa, fns[k]), "cudaFuncGetAttributes (static Gauss kernels)");
   }
-  *out = addr[dev];
+  if (st) return st;
+  *out = (double*)p;
   return GLASMA_OK;
 }
 

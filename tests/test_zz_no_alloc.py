@@ -84,6 +84,70 @@ def test_static_residual_matches_context_residual(G, precision, nc, nx, ny):
         assert ref[0] > 0 and ref[2] > 0
 
 
+def _windows_layout(G, h, dtype, with_b=True):
+    """The context's own charge windows (first slice and width from
+    glasma_get_info), with only those slices copied to the device."""
+    import torch
+    p = h.params
+    na = p.nc * p.nc - 1
+    info = G.glasma_get_info(h)
+    _, _, QA, QB, _ = G.glasma_get_fields(h)
+    out = []
+    for Q, (z0, W) in ((QA, info.window_a), (QB, info.window_b)):
+        if W == 0 or (Q is QB and not with_b):
+            out.append((None, 0, 0))
+            continue
+        q = np.moveaxis(Q.reshape(p.nz, p.ny * p.nx, na)[z0:z0 + W], 2, 0)
+        out.append((torch.from_numpy(np.ascontiguousarray(q)).to("cuda", dtype),
+                    z0, W))
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_static_residual_with_context_windows(G, precision):
+    """Narrow windows at their own offsets (the ka/kb arithmetic), then a
+    state without nucleus B (QB = NULL, WB = 0), each against
+    glasma_gauss_residual; the free device memory is the same before and
+    after a call."""
+    import torch
+    cfg = dict(gi.small_config(3, nx=7, ny=5), precision=precision)
+    h = G.glasma_init_mv(cfg, None)
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    p = h.params
+    stream = torch.cuda.current_stream()
+    G.glasma_step(h, 9)
+    ref = G.glasma_gauss_residual(h)
+    u, e, _, _ = _device_layout(G, h, dtype)
+    (qa, za, wa), (qb, zb, wb) = _windows_layout(G, h, dtype)
+    assert 0 < wa < p.nz and 0 < wb < p.nz and za > 0
+    args = (p.nc, precision, p.nz, p.ny, p.nx, p.a_t, p.a_z, u.data_ptr(),
+            e.data_ptr(), qa.data_ptr(), za, wa, qb.data_ptr(), zb, wb)
+    got = G.glasma_gauss_residual_static(*args, stream=stream)
+    for g, r in zip(got, ref):
+        assert abs(g - r) <= TOL * abs(r), (got, ref)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    got2 = G.glasma_gauss_residual_static(*args, stream=stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert got2 == got
+    # drop nucleus B from the context: its residual and the static one
+    # (QB = NULL, WB = 0) see the same charge density
+    U, E, QA, QB, n = G.glasma_get_fields(h)
+    G.glasma_set_fields(h, U, E, QA, np.zeros_like(QB), None, n)
+    assert G.glasma_get_info(h).window_b[1] == 0
+    ref = G.glasma_gauss_residual(h)
+    (qa, za, wa), (qb, zb, wb) = _windows_layout(G, h, dtype, with_b=False)
+    assert qb is None and wb == 0
+    got = G.glasma_gauss_residual_static(
+        p.nc, precision, p.nz, p.ny, p.nx, p.a_t, p.a_z, u.data_ptr(),
+        e.data_ptr(), qa.data_ptr(), za, wa, None, 0, 0, stream=stream)
+    for g, r in zip(got, ref):
+        assert abs(g - r) <= TOL * abs(r), (got, ref)
+    assert ref[0] > 1e-6      # the dropped charge violates Gauss's law
+
+
 def test_static_residual_rejects_oversized_lattice(G):
     with pytest.raises(G.GlasmaError) as e:
         G.glasma_gauss_residual_static(3, "fp64", 8193, 4, 4, 1.0, 1.0, 1, 1)
