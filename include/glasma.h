@@ -289,6 +289,38 @@ typedef struct {
 
 GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
 
+/* Kernels of the leapfrog step (the same update, Sec. 3 Eqs. lattice_1,
+ * plaquette, lattice_2, continuity, in two work decompositions):
+ *   GLASMA_KERNEL_STAPLE       one thread per link; each link sums its four
+ *                              staples U_{i,+-j} (every plaquette is formed
+ *                              once for each of its four links);
+ *   GLASMA_KERNEL_PLAQUETTE    one thread per transverse site marching along
+ *                              z; each plaquette is formed once and its
+ *                              projection, transported to each of its
+ *                              corners, goes to the four links it bounds
+ *                              (blocks of up to 320 threads);
+ *   GLASMA_KERNEL_PLAQUETTE_256  the same with blocks of up to 256 threads
+ *                              (more registers per thread);
+ *   GLASMA_KERNEL_AUTO         the default: the plaquette kernel for FP64
+ *                              state where a transverse row fits one block
+ *                              (nx <= 320; its 24% fewer FMAs win where the
+ *                              FP64 pipe bounds the step), else the staple
+ *                              kernel. */
+enum { GLASMA_KERNEL_AUTO = 0, GLASMA_KERNEL_STAPLE = 1, GLASMA_KERNEL_PLAQUETTE = 2,
+       GLASMA_KERNEL_PLAQUETTE_256 = 3 };
+
+/*
+ * Choose the leapfrog step kernel of a context and, for the plaquette
+ * kernel, the number of z slices each block marches through (zlen; 0 =
+ * automatic, about eight blocks per resident block slot).  Results of the
+ * two kernels agree to rounding (their sums run in different orders); the
+ * choice never changes the state's layout, so it may change between steps.
+ * Errors: INVALID_ARG (unknown kernel, zlen outside [0, nz], a plaquette
+ * kernel asked for on a lattice whose transverse rows do not fit one
+ * block).
+ */
+GLASMA_API int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen);
+
 /*
  * Rest-frame analysis of sampled tables (Sec. 4: the event average of
  * T^{mu nu}, its diagonalisation to the local rest-frame energy density

@@ -40,6 +40,9 @@ struct glasma_ctx {
   int* dflag = nullptr;       // device status word(s)
   int last_launches = 0;
   int last_iters = 0;
+  int step_kernel = 0;        // GLASMA_KERNEL_* of the leapfrog step
+  int step_zlen = 0;          // z slices per block of the plaquette kernel (0 = automatic)
+  bool plaq_ready = false;    // the plaquette kernel's attributes are set on this device
   struct Alloc {
     void* ptr;
     size_t bytes;
@@ -71,6 +74,15 @@ GL_HD bool hop_at(long long n, long long p, long long q) {
 
 // kernel launchers
 int launch_step_leapfrog(glasma_ctx* c, bool hop);
+// plaquette-centric leapfrog step (k_step_plaq.cu): zlen z slices per block
+int launch_step_plaq(glasma_ctx* c, bool hop, int zlen);
+bool plaq_fits(const glasma_ctx* c);
+// the step kernel glasma_step launches for this context: plaquette or staple
+bool use_plaq_kernel(const glasma_ctx* c);
+int plaq_default_zlen(const glasma_ctx* c);
+// set the plaquette kernel's function attributes for this context (before
+// any capture of its launches)
+int plaq_prepare(glasma_ctx* c);
 int launch_step_implicit(glasma_ctx* c, bool hop, int* iters);
 int launch_gauss(glasma_ctx* c, double* out3);
 // host_tab != NULL: read the table back and synchronise; dev_tab != NULL:

@@ -440,15 +440,22 @@ static int persistent_run(glasma_batch* b, int steps, int bx) {
 }
 
 // Per-event mode: the single-event step kernel of every event and step
-// captured into one graph (no batched kernel; for events that fill the GPU
-// on their own).  The contexts' streams and bookkeeping are pointed at the
-// capture while it runs and set back afterwards.
+// (the kernel glasma_step would use for that context) captured into one
+// graph (no batched kernel; for events that fill the GPU on their own).
+// The contexts' streams and bookkeeping are pointed at the capture while
+// it runs and set back afterwards.
+
 static int per_event_run(glasma_batch* b, int steps) {
   if (steps == 0) return GLASMA_OK;
   const size_t ne = b->ev.size();
   const EventCursor start(b);
   EventCursor cs(b);
-  int st = cuda_check(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "batch capture begin");
+  int st = GLASMA_OK;
+  // function attributes are set before the capture, not inside it
+  for (size_t e = 0; e < ne && !st; ++e)
+    if (use_plaq_kernel(b->ev[e])) st = plaq_prepare(b->ev[e]);
+  if (st) return st;
+  st = cuda_check(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "batch capture begin");
   if (st) return st;
   for (int k = 0; k < steps && !st; ++k) {
     for (size_t e = 0; e < ne && !st; ++e) {
@@ -457,7 +464,8 @@ static int per_event_run(glasma_batch* b, int steps) {
       c->cur = cs.cur[e];
       c->zA0 = cs.zA0[e];
       c->zB0 = cs.zB0[e];
-      st = launch_step_leapfrog(c, hop_at(cs.n[e], c->hop_p, c->hop_q));
+      const bool hop = hop_at(cs.n[e], c->hop_p, c->hop_q);
+      st = use_plaq_kernel(c) ? launch_step_plaq(c, hop, c->step_zlen) : launch_step_leapfrog(c, hop);
       c->stream = b->stream;
     }
     cs.advance(b);

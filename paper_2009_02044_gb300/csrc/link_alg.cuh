@@ -12,6 +12,8 @@
 //   ident, mul, mul_d (x y^+), d_mul (x^+ y)       products of links
 //   Sum, zero_sum, sum_add                          weighted staple sums
 //   proj_mul(u, S)                                  Im tr t^a (U S)
+//   proj_prod(x, y), proj_prod_d(x, y)              Im tr t^a (x y), (x y^+)
+//                                                   of two stored-form links
 //   expi(v, c)                                      exp(i c v^a t^a)
 //   reunit, adj (U q U^+), adj_dag (U^+ q U)
 #pragma once
@@ -35,6 +37,8 @@ struct LinkAlg<NC, double> : Group<NC, double> {
   GL_HD static Sum zero_sum() { return G::zero(); }
   GL_HD static void sum_add(Sum& s, double w, const M& t) { G::scale_add(s, w, t); }
   GL_HD static void proj_mul_sum(const M& u, const Sum& s, double* out) { G::proj_mul(u, s, out); }
+  GL_HD static void proj_prod(const M& x, const M& y, double* out) { G::proj_mul(x, y, out); }
+  GL_HD static void proj_prod_d(const M& x, const M& y, double* out) { G::proj_mul(x, G::dag(y), out); }
 };
 
 // ---------------------------------------------------------------------------
@@ -152,6 +156,17 @@ struct LinkAlg<3, float> {
   GL_HD static void proj_mul(const M& u, const M& x, R* o) {
     Sum s{0.f, x};
     proj_mul_sum(u, s, o);
+  }
+  // Im tr t^a (1+x)(1+y) and Im tr t^a (1+x)(1+y)^+ of two deviations:
+  // the staple-sum form with weight 1 and d = y (or y^+), so every
+  // rounding stays of the size u |x|, u |y|.
+  GL_HD static void proj_prod(const M& x, const M& y, R* o) {
+    Sum s{1.f, y};
+    proj_mul_sum(x, s, o);
+  }
+  GL_HD static void proj_prod_d(const M& x, const M& y, R* o) {
+    Sum s{1.f, G::dag(y)};
+    proj_mul_sum(x, s, o);
   }
 
   // exp(i c v^a t^a) - 1 by Cayley-Hamilton.  Q = c v^a t^a is hermitian and
@@ -397,6 +412,14 @@ struct LinkAlg<2, float> {
   GL_HD static void proj_mul(const M& u, const M& x, R* o) {
     Sum s{0.f, x};
     proj_mul_sum(u, s, o);
+  }
+  GL_HD static void proj_prod(const M& x, const M& y, R* o) {
+    Sum s{1.f, y};
+    proj_mul_sum(x, s, o);
+  }
+  GL_HD static void proj_prod_d(const M& x, const M& y, R* o) {
+    Sum s{1.f, dag(y)};
+    proj_mul_sum(x, s, o);
   }
   // exp(i c v.sigma/2) - 1 = (cos th - 1 + i sin th n3, sin th (n2 + i n1)),
   // cos th - 1 = -2 sin^2(th/2)

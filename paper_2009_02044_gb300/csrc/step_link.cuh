@@ -21,25 +21,23 @@ struct StepArgs {
   int zA0, WA, zB0, WB;
 };
 
-// Link i of the site with transverse index t on slice iz:
+// Steps (1)-(3) below for link i of the site s = iz*nxy + t, given the
+// staple force F (Eq. lattice_1 without the dt):
 //   (1) on a hop step, for the z link: transport the charge of B at x to
 //       x+z (Q' = U_z^dag Q U_z) and the charge of A at x+z to x
 //       (Q' = U_z Q U_z^dag) in their co-moving slots, and deposit
 //       dt J_z = a_z^2 (Q'_A - Q_B) (the current of the continuity equation
 //       with Gauss weights 1/a_i^2);
-//   (2) add dt times the staple force to E;
+//   (2) E += dt F (+ dt J on the z link);
 //   (3) write exp(i dt E) U to the other link buffer (re-unitarised in FP32).
+// Shared by the staple kernel below and the plaquette kernel
+// (k_step_plaq.cu), so both apply the same update arithmetic.
 template <int NC, typename R>
-__device__ __forceinline__ void step_link(const StepArgs<R>& a, int i, uint32_t t, int iz) {
+__device__ __forceinline__ void update_link(const StepArgs<R>& a, int i, uint32_t t, int iz, int64_t s,
+                                            const R* F) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  if (t >= (uint32_t)a.g.nxy) return;
-  if (i == 2 && iz == a.g.nz - 1) return;  // no z link on the last slice
-  const SiteNbr n = site_nbr_tz(a.g, t, iz);
-  const int64_t s = n.s;
-  R F[NA];
-  link_force_staple<NC, R, R>(a.U, a.g, n, i, a.w, F);
   const M Ui = LinkIO<NC, R>::template load<R>(a.U, i, a.g.V, s);
   R e[NA];
 #pragma unroll
@@ -48,7 +46,7 @@ __device__ __forceinline__ void step_link(const StepArgs<R>& a, int i, uint32_t 
     R dj[NA];
 #pragma unroll
     for (int c = 0; c < NA; ++c) dj[c] = R(0);
-    const int kb = n.iz - a.zB0;
+    const int kb = iz - a.zB0;
     if (kb >= 0 && kb < a.WB) {
       R q[NA];
 #pragma unroll
@@ -59,7 +57,7 @@ __device__ __forceinline__ void step_link(const StepArgs<R>& a, int i, uint32_t 
 #pragma unroll
       for (int c = 0; c < NA; ++c) a.QB[((int64_t)c * a.WB + kb) * a.g.nxy + t] = q[c];
     }
-    const int ka = n.iz + 1 - a.zA0;
+    const int ka = iz + 1 - a.zA0;
     if (ka >= 0 && ka < a.WA) {
       R q[NA];
 #pragma unroll
@@ -79,6 +77,20 @@ __device__ __forceinline__ void step_link(const StepArgs<R>& a, int i, uint32_t 
   M un = G::mul(G::expi(e, a.dt), Ui);
   if (sizeof(R) == 4) un = G::reunit(un);
   LinkIO<NC, R>::template store<R>(a.Un, i, a.g.V, s, un);
+}
+
+// Link i of the site with transverse index t on slice iz, its force from
+// the four staples (link_force_staple); the z link of the last slice does
+// not exist.
+template <int NC, typename R>
+__device__ __forceinline__ void step_link(const StepArgs<R>& a, int i, uint32_t t, int iz) {
+  constexpr int NA = LinkAlg<NC, R>::NA;
+  if (t >= (uint32_t)a.g.nxy) return;
+  if (i == 2 && iz == a.g.nz - 1) return;  // no z link on the last slice
+  const SiteNbr n = site_nbr_tz(a.g, t, iz);
+  R F[NA];
+  link_force_staple<NC, R, R>(a.U, a.g, n, i, a.w, F);
+  update_link<NC, R>(a, i, t, iz, n.s, F);
 }
 
 }  // namespace glasma

@@ -24,6 +24,7 @@ ERRORS = {
 }
 FP64, FP32 = 0, 1
 LEAPFROG, IMPLICIT = 0, 1
+KERNELS = {"auto": 0, "staple": 1, "plaquette": 2, "plaquette_256": 3}
 
 
 class GlasmaError(RuntimeError):
@@ -92,6 +93,7 @@ def load_library(path=LIB_PATH):
         "glasma_get_state": (C.c_int, [P, P, C.c_size_t]),
         "glasma_set_state": (C.c_int, [P, P, C.c_size_t]),
         "glasma_get_info": (C.c_int, [P, C.POINTER(glasma_info)]),
+        "glasma_set_step_kernel": (C.c_int, [P, C.c_int, C.c_int]),
         "glasma_gauss_residual_static": (
             C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                       C.c_double, C.c_double, P, P, P, C.c_int, C.c_int, P,
@@ -332,6 +334,15 @@ def glasma_get_info(h):
     _check(load_library().glasma_get_info(h.ptr, C.byref(info)),
            "glasma_get_info")
     return info
+
+
+def glasma_set_step_kernel(h, kernel="auto", zlen=0):
+    """Leapfrog step kernel of the context: "auto", "staple", "plaquette"
+    or "plaquette_256"; zlen = z slices per block of the plaquette kernel
+    (0 = automatic)."""
+    _check(load_library().glasma_set_step_kernel(h.ptr, KERNELS[kernel],
+                                                 int(zlen)),
+           "glasma_set_step_kernel")
 
 
 def glasma_free(h):

@@ -1,8 +1,9 @@
 """GPU tests of the batched ensemble (glasma_batch_*): several independent
 events of uneven lattice size advanced by one kernel per step must give
-each event bitwise the state it gets alone from glasma_step (the same
-per-link arithmetic) in every execution mode, and one batched event must
-match the FP64 oracle."""
+each event bitwise the state it gets alone from glasma_step with the same
+step kernel (the batched graph and persistent modes run the staple kernel's
+per-link arithmetic; the per-event mode launches each context's own
+kernel), and one batched event must match the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,13 @@ def _cfgs(nc, precision):
             for k, (nz, nx, ny) in enumerate(SIZES)]
 
 
+def _match_kernel(G, hs, mode):
+    """Single-event references run the kernel the batch mode runs: the
+    staple kernel for the batched graph and persistent modes."""
+    for h in hs:
+        G.glasma_set_step_kernel(h, "auto" if mode == "per_event" else "staple")
+
+
 def _same(G, h1, h2):
     a = G.glasma_get_fields(h1)
     b = G.glasma_get_fields(h2)
@@ -49,6 +57,7 @@ def test_batch_is_bitwise_the_single_event_step(G, nc, precision, mode):
     cfgs = _cfgs(nc, precision)
     single = [G.glasma_init_mv(c, None) for c in cfgs]
     batched = [G.glasma_init_mv(c, None) for c in cfgs]
+    _match_kernel(G, single, mode)
     b = G.glasma_batch_create(batched)
     G.glasma_batch_set_shape(b, mode, 64)
     G.glasma_batch_step(b, 7)      # two calls: bookkeeping carried over
@@ -68,6 +77,7 @@ def test_every_block_shape_is_bitwise(G, mode, block_sites):
     cfgs = _cfgs(3, "fp32")
     single = [G.glasma_init_mv(c, None) for c in cfgs]
     batched = [G.glasma_init_mv(c, None) for c in cfgs]
+    _match_kernel(G, single, mode)
     b = G.glasma_batch_create(batched)
     G.glasma_batch_set_shape(b, mode, block_sites)
     G.glasma_batch_step(b, 11)
@@ -102,6 +112,7 @@ def test_tune_keeps_the_state_and_the_result(G, precision):
     b = G.glasma_batch_create(batched)
     bx, mode = G.glasma_batch_tune(b, 4)
     assert bx in (32, 64, 128) and mode in G.BATCH_MODES
+    _match_kernel(G, single, mode)
     for h1, h2 in zip(single, batched):
         _same(G, h1, h2)            # tuning left every event as it was
     G.glasma_batch_step(b, 9)
@@ -128,6 +139,7 @@ def test_particle_exit_stops_every_event_at_the_same_step(G, mode):
     for c, h in zip((short, long_), hs):
         assert G.glasma_get_info(h).step_n == n_exit
         ref = G.glasma_init_mv(c, None)
+        _match_kernel(G, [ref], mode)
         G.glasma_step(ref, n_exit)
         _same(G, ref, h)
 
@@ -165,6 +177,7 @@ def test_barrier_wait_that_runs_out_returns_timeout(G):
         G.glasma_set_state(h, blob)
     G.glasma_batch_step(b, 5)
     ref = [G.glasma_init_mv(c, None) for c in cfgs]
+    _match_kernel(G, ref, "persistent")
     for h1, h2 in zip(ref, hs):
         G.glasma_step(h1, 5)
         _same(G, h1, h2)
@@ -178,6 +191,7 @@ def test_persistent_call_longer_than_one_launch(G):
             for k, (nz, nx, ny) in enumerate([(200, 9, 8), (208, 16, 4)])]
     single = [G.glasma_init_mv(c, None) for c in cfgs]
     batched = [G.glasma_init_mv(c, None) for c in cfgs]
+    _match_kernel(G, single, "persistent")
     b = G.glasma_batch_create(batched)
     G.glasma_batch_set_shape(b, "persistent", 64)
     G.glasma_batch_step(b, 150)

@@ -1,0 +1,153 @@
+"""The two leapfrog step kernels (staple form and plaquette-centric form,
+glasma_set_step_kernel) against the FP64 oracle, through the C ABI.
+
+The plaquette kernel splits the lattice into blocks of whole transverse rows
+with a -y halo row, marching through z in chunks with a warm-up slice; the
+cases below cover a block that holds the whole plane (no halo), blocks whose
+row count divides ny, a ragged last block (ny prime), the 64 x 64 transverse
+plane of the SU(3) 512 x 64^2 workload, chunks of one slice and chunks that
+cross the collision, and both block shapes.  Tolerance: the FP64 target,
+1e-11 relative to the largest reference entry."""
+import numpy as np
+import pytest
+
+import glasma_inputs as gi
+from oracle import glasma_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+KERNELS = ["staple", "plaquette", "plaquette_256"]
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_02044_gb300 import build as B
+    B.build()
+    from paper_2009_02044_gb300 import glasma
+    glasma.load_library()
+    return glasma
+
+
+def rel(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def _random_state(nc, nz, ny, nx, seed):
+    """Generic links (near the identity, amplitude 0.3), fields and charges
+    of both nuclei, so every plaquette orientation and both hop directions
+    carry O(1) contributions."""
+    rng = np.random.default_rng(seed)
+    p = O.Params(nc=nc, nz=nz, nx=nx, ny=ny, a_z=0.5, dt=0.25, sigma_l=1.0)
+    na = nc * nc - 1
+    U = gi.near_identity_su(nc, (3, nz, ny, nx), rng, 0.3)
+    U[2][nz - 1] = np.eye(nc)
+    E = 0.3 * rng.standard_normal((3, nz, ny, nx, na))
+    E[2][nz - 1] = 0.0
+    QA = np.zeros((nz, ny, nx, na))
+    QB = np.zeros((nz, ny, nx, na))
+    QA[nz // 2 + 1: nz - 2] = 0.1 * rng.standard_normal(QA[nz // 2 + 1: nz - 2].shape)
+    QB[2: nz // 2 - 1] = 0.1 * rng.standard_normal(QB[2: nz // 2 - 1].shape)
+    return O.State(p, U, E, QA, QB, 0, U.copy())
+
+
+def _ctx(G, st, precision="fp64"):
+    p = st.p
+    # a placeholder event (no charge, thin nuclei that fit a short box);
+    # set_fields then replaces its whole state
+    cfg = dict(nc=p.nc, nz=p.nz, nx=p.nx, ny=p.ny, a_t=1.0, a_z=p.a_z,
+               dt=p.dt, sigma_l=0.05, z_offset=0.3, g2mu=0.0, m_ir=0.2,
+               seed=0, precision=precision)
+    h = G.glasma_init_mv(cfg, None)
+    G.glasma_set_fields(h, st.U, st.E, st.QA, st.QB, None, st.n)
+    return h
+
+
+# (nz, ny, nx): whole plane in one block; rows dividing ny; ny prime
+# (ragged last block); the 64 x 64 plane of the throughput workload
+SHAPES = [(12, 6, 13), (10, 40, 17), (9, 37, 17), (8, 64, 64)]
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_kernel_matches_oracle_on_random_state(G, nc, shape, kernel):
+    nz, ny, nx = shape
+    st = _random_state(nc, nz, ny, nx, seed=7 * nz + ny + nc)
+    ref = O.step(st, 3)                  # hops at steps 0 and 2
+    for zlen in ([0] if kernel == "staple" else [0, 1, 3, nz]):
+        h = _ctx(G, st)
+        G.glasma_set_step_kernel(h, kernel, zlen)
+        G.glasma_step(h, 3)
+        U, E, QA, QB, n = G.glasma_get_fields(h)
+        assert n == 3
+        errs = dict(U=rel(U, ref.U), E=rel(E, ref.E), QA=rel(QA, ref.QA),
+                    QB=rel(QB, ref.QB))
+        assert all(v <= TOL64 for v in errs.values()), (kernel, zlen, errs)
+        G.glasma_free(h)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_kernels_agree(G, kernel):
+    """FP32 state: each kernel against the FP64 oracle on a random SU(3)
+    state with the 64 x 64 plane.  Bound: per step E and U round at
+    u = 6e-8 relative to O(1) entries, and the four plaquette
+    contributions of a link sum a few such roundings; 3 steps stay below
+    3 * 8 * u ~ 1.5e-6 of the largest entry."""
+    st = _random_state(3, 8, 64, 64, seed=99)
+    ref = O.step(st, 3)
+    h = _ctx(G, st, "fp32")
+    G.glasma_set_step_kernel(h, kernel)
+    G.glasma_step(h, 3)
+    U, E, QA, QB, n = G.glasma_get_fields(h)
+    assert rel(U, ref.U) < 1.5e-6 and rel(E, ref.E) < 1.5e-6
+    assert rel(QA, ref.QA) < 1.5e-6 and rel(QB, ref.QB) < 1.5e-6
+
+
+def test_su3_64x64_collision_fp64_full_state(G):
+    """SU(3) with the 64 x 64 transverse plane of the throughput workload,
+    FP64, 20 steps through the collision (sigma_L = a, nuclei meet after 12
+    steps), the whole state (U, E, Q_A, Q_B) and eps(z) against the oracle
+    at every step count it passes: full 64-site rows and full 32-site link
+    blocks are the norm here, not the ragged exception."""
+    cfg = gi.small_config(3, nz=28, nx=64, ny=64, sigma_l=1.0, steps=20)
+    p = O.Params.from_dict(cfg)
+    rho = gi.mv_rho(cfg["seed"], 3, p.nx, p.ny, p.g2mu)
+    st = O.init_mv(p, rho)
+    h = G.glasma_init_mv(cfg, rho)
+    for block in (6, 6, 8):
+        G.glasma_step(h, block)
+        st = O.step(st, block)
+        U, E, QA, QB, n = G.glasma_get_fields(h)
+        assert n == st.n
+        errs = dict(U=rel(U, st.U), E=rel(E, st.E), QA=rel(QA, st.QA),
+                    QB=rel(QB, st.QB))
+        tab, H = G.glasma_tmunu(h)
+        rtab, rH = O.tmunu(st)
+        errs["eps"] = rel(tab[:, 0], rtab[:, 0])
+        errs["H"] = abs(H - rH) / abs(rH)
+        assert all(v <= TOL64 for v in errs.values()), (n, errs)
+    # the nuclei have crossed: charge of B beyond the centre
+    _, _, zc = O.nucleus_positions(p)
+    z = np.arange(p.nz) * p.a_z
+    assert np.any(np.abs(st.QB[z > zc]) > 0)
+    gmax, grms, rmax = G.glasma_gauss_residual(h)
+    assert gmax <= 1e-12 * rmax
+
+
+def test_set_step_kernel_rejects_bad_arguments(G):
+    h = G.glasma_init_mv(gi.small_config(2), None)
+    for kernel, zlen in ((7, 0), (1, -1), (2, 10 ** 6)):
+        with pytest.raises(G.GlasmaError) as e:
+            G._check(G.load_library().glasma_set_step_kernel(h.ptr, kernel, zlen),
+                     "glasma_set_step_kernel")
+        assert e.value.code == "INVALID_ARG"
+    # rows longer than a block take no plaquette kernel
+    wide = G.glasma_init_mv(gi.small_config(2, nz=24, nx=400, ny=2, sigma_l=1.0), None)
+    with pytest.raises(G.GlasmaError):
+        G.glasma_set_step_kernel(wide, "plaquette")
+    G.glasma_set_step_kernel(wide, "auto")
+    G.glasma_step(wide, 2)            # auto falls back to the staple kernel
