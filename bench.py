@@ -71,6 +71,12 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--nz", type=int, default=0,
                     help="override the lattice length (profiling on a smaller case)")
+    ap.add_argument("--kernel", default="auto",
+                    choices=["auto", "staple", "staple_pairs", "plaquette",
+                             "plaquette_256"],
+                    help="leapfrog step kernel (glasma_set_step_kernel)")
+    ap.add_argument("--zlen", type=int, default=0,
+                    help="z slices per block of the plaquette kernel (0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, e2e and error check")
@@ -100,9 +106,20 @@ def step_kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2009_02044_gb300", "csrc")
     for f in ("k_step.cu", "step_link.cuh", "link_alg.cuh", "lattice.cuh",
-              "su_n.cuh"):
+              "su_n.cuh", "step_pair.cuh", "pair.cuh", "k_step_plaq.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def step_kernel_name(nc, precision, kernel):
+    """The CUDA kernel glasma_step launches for this choice (the library's
+    automatic choice: plaquette kernel in FP64, staple kernel on site pairs
+    for SU(2) FP32, one-site staple kernel for SU(3) FP32)."""
+    if kernel == "auto":
+        kernel = ("plaquette" if precision == "fp64" else
+                  "staple_pairs" if nc == 2 else "staple")
+    return {"staple": "k_step_leapfrog", "staple_pairs": "k_step_pair",
+            "plaquette": "k_step_plaq", "plaquette_256": "k_step_plaq"}[kernel]
 
 
 def load_peaks():
@@ -320,6 +337,7 @@ def run_ours(args, cfg):
 
     with torch.cuda.stream(stream):
         h = G.glasma_init_mv(cfg, None, stream=stream)
+    G.glasma_set_step_kernel(h, args.kernel, args.zlen)
     G.glasma_step(h, W)
     info = G.glasma_get_info(h)
     state_bytes = info.state_device_bytes
@@ -359,7 +377,8 @@ def run_ours(args, cfg):
     traffic = prof["dram_bytes_per_launch"] if prof else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-            "kernel": "k_step_leapfrog", "peak_source": peak_kind,
+            "kernel": step_kernel_name(nc, args.precision, args.kernel),
+            "peak_source": peak_kind,
             "alg_bytes_per_launch": alg}
     if prof and prof.get("ffma_per_launch"):
         # the FP32 FMA pipe next to HBM: the kernel's FFMA count (ncu) over

@@ -301,13 +301,19 @@ GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
  *                              (blocks of up to 320 threads);
  *   GLASMA_KERNEL_PLAQUETTE_256  the same with blocks of up to 256 threads
  *                              (more registers per thread);
- *   GLASMA_KERNEL_AUTO         the default: the plaquette kernel for FP64
- *                              state where a transverse row fits one block
- *                              (nx <= 320; its 24% fewer FMAs win where the
- *                              FP64 pipe bounds the step), else the staple
- *                              kernel. */
+ *   GLASMA_KERNEL_STAPLE_PAIRS the staple kernel on two sites per thread,
+ *                              (x, y, z) and (x, y, z + ceil(nz/2)), in the
+ *                              two lanes of the packed FP32 instructions
+ *                              (FP32 state only);
+ *   GLASMA_KERNEL_AUTO         the default, from GB300 timings: for FP64
+ *                              state the plaquette kernel where a transverse
+ *                              row fits one block (nx <= 320; its 24% fewer
+ *                              FMAs win where the FP64 pipe bounds the
+ *                              step), else the staple kernel; for FP32 the
+ *                              staple kernel (SU(3)) or the paired staple
+ *                              kernel (SU(2)). */
 enum { GLASMA_KERNEL_AUTO = 0, GLASMA_KERNEL_STAPLE = 1, GLASMA_KERNEL_PLAQUETTE = 2,
-       GLASMA_KERNEL_PLAQUETTE_256 = 3 };
+       GLASMA_KERNEL_PLAQUETTE_256 = 3, GLASMA_KERNEL_STAPLE_PAIRS = 4 };
 
 /*
  * Choose the leapfrog step kernel of a context and, for the plaquette
@@ -317,7 +323,7 @@ enum { GLASMA_KERNEL_AUTO = 0, GLASMA_KERNEL_STAPLE = 1, GLASMA_KERNEL_PLAQUETTE
  * choice never changes the state's layout, so it may change between steps.
  * Errors: INVALID_ARG (unknown kernel, zlen outside [0, nz], a plaquette
  * kernel asked for on a lattice whose transverse rows do not fit one
- * block).
+ * block, the paired kernel asked for on FP64 state).
  */
 GLASMA_API int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen);
 

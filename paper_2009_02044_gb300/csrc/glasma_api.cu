@@ -128,15 +128,27 @@ static int check_params(const glasma_params* p) {
   return GLASMA_OK;
 }
 
-// The automatic choice, from CUDA-event timings of the SU(3) 512 x 64^2
-// workload on GB300: the plaquette kernel needs 24% fewer FMAs, which wins
-// where the FP64 pipe bounds the step (12.8 against 15.3 ms); in FP32 the
-// staple kernel issues fewer non-FMA instructions and needs no barriers
-// (0.469 against 0.518 ms).
+// The automatic choice, from CUDA-event timings on GB300: in FP64 the
+// plaquette kernel (24% fewer FMAs, and the FP64 pipe bounds the step:
+// 12.8 against 15.3 ms per SU(3) 512 x 64^2 step); in FP32 SU(3) the
+// one-site staple kernel (0.469 ms, against 0.521 for the plaquette kernel
+// and 0.572 for site pairs, whose 168 registers leave too few warps to hide
+// latency); in FP32 SU(2) site pairs (1.17 against 1.22 ms per
+// 1024 x 128^2 step).
 bool use_plaq_kernel(const glasma_ctx* c) {
-  if (c->step_kernel == GLASMA_KERNEL_STAPLE) return false;
-  if (c->step_kernel == GLASMA_KERNEL_AUTO && c->rs != 8) return false;
-  return plaq_fits(c);
+  if (c->step_kernel == GLASMA_KERNEL_PLAQUETTE || c->step_kernel == GLASMA_KERNEL_PLAQUETTE_256) return plaq_fits(c);
+  return c->step_kernel == GLASMA_KERNEL_AUTO && c->rs == 8 && plaq_fits(c);
+}
+
+bool use_pair_kernel(const glasma_ctx* c) {
+  if (c->rs != 4) return false;
+  return c->step_kernel == GLASMA_KERNEL_STAPLE_PAIRS || (c->step_kernel == GLASMA_KERNEL_AUTO && c->p.nc == 2);
+}
+
+int launch_step_chosen(glasma_ctx* c, bool hop) {
+  if (use_plaq_kernel(c)) return launch_step_plaq(c, hop, c->step_zlen);
+  if (use_pair_kernel(c)) return launch_step_pair(c, hop);
+  return launch_step_leapfrog(c, hop);
 }
 
 }  // namespace glasma
@@ -258,10 +270,7 @@ int glasma_step(glasma_ctx* c, int n_steps) {
       c->last_iters = iters;
       launches += iters + 1;
     } else {
-      if (use_plaq_kernel(c))
-        st = launch_step_plaq(c, hop, c->step_zlen);
-      else
-        st = launch_step_leapfrog(c, hop);
+      st = launch_step_chosen(c, hop);
       launches += 1;
     }
     // a step that did not converge has still been taken (last iterate kept)
@@ -734,8 +743,10 @@ int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes) {
 int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen) {
   if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
   if (kernel != GLASMA_KERNEL_AUTO && kernel != GLASMA_KERNEL_STAPLE && kernel != GLASMA_KERNEL_PLAQUETTE &&
-      kernel != GLASMA_KERNEL_PLAQUETTE_256)
+      kernel != GLASMA_KERNEL_PLAQUETTE_256 && kernel != GLASMA_KERNEL_STAPLE_PAIRS)
     return set_error(GLASMA_ERR_INVALID_ARG, "unknown step kernel");
+  if (kernel == GLASMA_KERNEL_STAPLE_PAIRS && c->rs != 4)
+    return set_error(GLASMA_ERR_INVALID_ARG, "the paired staple kernel needs FP32 state");
   if (zlen < 0 || zlen > c->g.nz) return set_error(GLASMA_ERR_INVALID_ARG, "zlen must be in [0, nz]");
   const int old = c->step_kernel;
   c->step_kernel = kernel;

@@ -77,8 +77,13 @@ int launch_step_leapfrog(glasma_ctx* c, bool hop);
 // plaquette-centric leapfrog step (k_step_plaq.cu): zlen z slices per block
 int launch_step_plaq(glasma_ctx* c, bool hop, int zlen);
 bool plaq_fits(const glasma_ctx* c);
-// the step kernel glasma_step launches for this context: plaquette or staple
+// the step kernel glasma_step launches for this context: plaquette, staple
+// on site pairs (FP32) or staple
 bool use_plaq_kernel(const glasma_ctx* c);
+bool use_pair_kernel(const glasma_ctx* c);
+int launch_step_chosen(glasma_ctx* c, bool hop);
+// staple kernel on pairs of sites (t, iz), (t, iz + ceil(nz/2)), FP32 only
+int launch_step_pair(glasma_ctx* c, bool hop);
 int plaq_default_zlen(const glasma_ctx* c);
 // set the plaquette kernel's function attributes for this context (before
 // any capture of its launches)

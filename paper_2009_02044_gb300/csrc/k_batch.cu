@@ -465,7 +465,7 @@ static int per_event_run(glasma_batch* b, int steps) {
       c->zA0 = cs.zA0[e];
       c->zB0 = cs.zB0[e];
       const bool hop = hop_at(cs.n[e], c->hop_p, c->hop_q);
-      st = use_plaq_kernel(c) ? launch_step_plaq(c, hop, c->step_zlen) : launch_step_leapfrog(c, hop);
+      st = launch_step_chosen(c, hop);
       c->stream = b->stream;
     }
     cs.advance(b);

@@ -16,8 +16,42 @@
 //                                                   of two stored-form links
 //   expi(v, c)                                      exp(i c v^a t^a)
 //   reunit, adj (U q U^+), adj_dag (U^+ q U)
+//
+// The FP32 forms are templates over the lane type T: float (one site per
+// thread) or f2 (pair.cuh: two sites per thread in the lanes of the packed
+// f32x2 instructions).  With T = float every expression is the scalar one.
 #pragma once
 #include "su_n.cuh"
+#ifdef __CUDACC__
+#include "pair.cuh"
+#endif
+
+namespace glasma {
+// fma for the scalar lane types, visible next to the f2 overload of the
+// same name (which would otherwise hide the global ones in this namespace)
+GL_HD float fma(float a, float b, float c) { return fmaf(a, b, c); }
+GL_HD double fma(double a, double b, double c) { return ::fma(a, b, c); }
+// lane helpers for T = float (pair.cuh has the f2 forms)
+GL_HD bool all_zero_s(float a) { return a == 0.f; }
+GL_HD bool any_gt_s(float a, float b) { return a > b; }
+GL_HD bool all_abs_lt_s(float a, float b) { return fabsf(a) < b; }
+GL_HD float lane_abs_s(float a) { return fabsf(a); }
+GL_HD float lane_div_s(float a, float b) { return a / b; }
+// a / b, and 0 in a lane where b = 0 (a scalar caller has returned before)
+GL_HD float lane_div0_s(float a, float b) { return a / b; }
+#ifdef __CUDACC__
+__device__ __forceinline__ bool all_zero_s(f2 a) { return all_zero(a); }
+__device__ __forceinline__ bool any_gt_s(f2 a, float b) { return any_gt(a, b); }
+__device__ __forceinline__ bool all_abs_lt_s(f2 a, float b) { return all_abs_lt(a, b); }
+__device__ __forceinline__ f2 lane_abs_s(f2 a) { return lane_abs(a); }
+__device__ __forceinline__ f2 lane_div_s(f2 a, f2 b) { return lane_div(a, b); }
+__device__ __forceinline__ f2 lane_div0_s(f2 a, f2 b) {
+  return f2(b.v.x != 0.f ? a.v.x / b.v.x : 0.f, b.v.y != 0.f ? a.v.y / b.v.y : 0.f);
+}
+__device__ __forceinline__ f2 gl_sqrt(f2 x) { return lane_sqrt(x); }
+__device__ __forceinline__ void gl_sincos(f2 x, f2* s, f2* c) { *s = lane_sincos_s(x, c); }
+#endif
+}  // namespace glasma
 
 namespace glasma {
 
@@ -44,11 +78,11 @@ struct LinkAlg<NC, double> : Group<NC, double> {
 // ---------------------------------------------------------------------------
 // SU(3), FP32, deviation form: M holds d = U - 1 (row major).
 // ---------------------------------------------------------------------------
-template <>
-struct LinkAlg<3, float> {
-  typedef float R;
-  typedef Group<3, float> G;
-  typedef G::M M;
+template <typename T>
+struct LinkAlgDev3 {
+  typedef T R;
+  typedef Group<3, T> G;
+  typedef typename G::M M;
   static constexpr int NA = 8;
   static constexpr bool kDelta = true;
 
@@ -183,10 +217,10 @@ struct LinkAlg<3, float> {
 #pragma unroll
     for (int a = 0; a < NA; ++a) nq2 += v[a] * v[a];
     R nn = 0.5f * c * c * nq2;  // ||Q||_F^2
-    if (nn == 0.f) return G::zero();
+    if (all_zero_s(nn)) return G::zero();
     int s = 0;
     R sc = c;
-    while (nn > 0.25f && s < 40) {
+    while (any_gt_s(nn, 0.25f) && s < 40) {
       nn *= 0.25f;
       sc *= 0.5f;
       ++s;
@@ -220,15 +254,15 @@ struct LinkAlg<3, float> {
     // series: n = 1 gives i Q; n >= 2 by the recurrence
     R al = 0.f, be = 1.f, ga = 0.f;
     cplx<R> f0{0.f, 0.f}, f1{0.f, 1.f}, f2{0.f, 0.f};
-    const R inv_fact[10] = {1.f, 1.f, 0.5f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f, 1.f / 720.f, 1.f / 5040.f,
-                            1.f / 40320.f, 1.f / 362880.f};
+    const float inv_fact[10] = {1.f, 1.f, 0.5f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f, 1.f / 720.f, 1.f / 5040.f,
+                                1.f / 40320.f, 1.f / 362880.f};
 #pragma unroll
     for (int n = 2; n <= 9; ++n) {
       const R nal = c0 * ga, nbe = fma(c1, ga, al);
       ga = be;
       al = nal;
       be = nbe;
-      const R k = inv_fact[n];
+      const float k = inv_fact[n];
       // i^n: n mod 4 = 0: +1, 1: +i, 2: -1, 3: -i
       if ((n & 3) == 0) {
         f0.re = fma(k, al, f0.re); f1.re = fma(k, be, f1.re); f2.re = fma(k, ga, f2.re);
@@ -269,11 +303,11 @@ struct LinkAlg<3, float> {
     R nq2 = 0.f;
 #pragma unroll
     for (int a = 0; a < NA; ++a) nq2 += v[a] * v[a];
-    R nq = fabsf(c) * gl_sqrt(0.5f * nq2);
-    if (nq == 0.f) return G::zero();
+    R nq = lane_abs_s(c) * gl_sqrt(0.5f * nq2);
+    if (all_zero_s(nq)) return G::zero();
     int s = 0;
     R sc = c;
-    while (nq > 0.03125f && s < 40) {
+    while (any_gt_s(nq, 0.03125f) && s < 40) {
       nq *= 0.5f;
       sc *= 0.5f;
       ++s;
@@ -292,7 +326,7 @@ struct LinkAlg<3, float> {
 #pragma unroll
     for (int k = 3; k >= 2; --k) {
       const M QY = G::mul(Q, Y);
-      const R f = 1.f / (R)k;
+      const float f = 1.f / (float)k;
 #pragma unroll
       for (int q = 0; q < 9; ++q) Y.m[q] = cplx<R>{-f * QY.m[q].im, f * QY.m[q].re};
       Y.m[0].re += 1.f;
@@ -316,9 +350,9 @@ struct LinkAlg<3, float> {
   GL_HD static R inv_sqrt_m1(R eps) {  // 1/sqrt(1+eps) - 1
     // a link one step from the group has |eps| ~ 1e-7: the binomial series
     // -eps/2 + 3 eps^2/8 - 5 eps^3/16 is exact to 35/128 eps^4 there
-    if (fabsf(eps) < 1e-3f) return eps * fma(eps, fma(eps, -0.3125f, 0.375f), -0.5f);
-    const R r = gl_sqrt(1.f + eps);
-    return -eps / (r * (1.f + r));
+    if (all_abs_lt_s(eps, 1e-3f)) return eps * fma(eps, fma(eps, R(-0.3125f), R(0.375f)), R(-0.5f));
+    const R r = gl_sqrt(R(1.f) + eps);
+    return lane_div_s(-eps, r * (R(1.f) + r));
   }
   GL_HD static M reunit(const M& x) {
     M r;
@@ -369,14 +403,17 @@ struct LinkAlg<3, float> {
   GL_HD static void adj_dag(const M& u, R* q) { G::adj_dag(full(u), q); }
 };
 
+template <>
+struct LinkAlg<3, float> : LinkAlgDev3<float> {};
+
 // ---------------------------------------------------------------------------
 // SU(2), FP32, deviation form: M = (alpha - 1, beta).
 // ---------------------------------------------------------------------------
-template <>
-struct LinkAlg<2, float> {
-  typedef float R;
-  typedef Group<2, float> G;
-  typedef G::M M;
+template <typename T>
+struct LinkAlgDev2 {
+  typedef T R;
+  typedef Group<2, T> G;
+  typedef typename G::M M;
   static constexpr int NA = 3;
   static constexpr bool kDelta = true;
 
@@ -425,20 +462,25 @@ struct LinkAlg<2, float> {
   // cos th - 1 = -2 sin^2(th/2)
   GL_HD static M expi(const R* v, R c) {
     const R n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    if (n2 == 0.f) return G::zero();
+    if (all_zero_s(n2)) return G::zero();
     const R nrm = gl_sqrt(n2);
     R sh, ch;
     gl_sincos(0.25f * c * nrm, &sh, &ch);  // half of th = c |v| / 2
-    const R s = 2.f * sh * ch, f = s / nrm;
+    // a lane whose field is zero while its partner's is not has nrm = 0
+    // and v = 0: its factor is set to 0
+    const R s = 2.f * sh * ch, f = lane_div0_s(s, nrm);
     return M{{-2.f * sh * sh, f * v[2]}, {f * v[1], f * v[0]}};
   }
   GL_HD static M reunit(const M& x) {
     const R eps = 2.f * x.a.re + x.a.re * x.a.re + x.a.im * x.a.im + x.b.re * x.b.re + x.b.im * x.b.im;
-    const R r = gl_sqrt(1.f + eps), g = -eps / (r * (1.f + r)), f = 1.f + g;
+    const R r = gl_sqrt(R(1.f) + eps), g = lane_div_s(-eps, r * (R(1.f) + r)), f = R(1.f) + g;
     return M{{g + f * x.a.re, f * x.a.im}, f * x.b};
   }
   GL_HD static void adj(const M& u, R* q) { G::adj(full(u), q); }
   GL_HD static void adj_dag(const M& u, R* q) { G::adj_dag(full(u), q); }
 };
+
+template <>
+struct LinkAlg<2, float> : LinkAlgDev2<float> {};
 
 }  // namespace glasma

@@ -24,7 +24,8 @@ ERRORS = {
 }
 FP64, FP32 = 0, 1
 LEAPFROG, IMPLICIT = 0, 1
-KERNELS = {"auto": 0, "staple": 1, "plaquette": 2, "plaquette_256": 3}
+KERNELS = {"auto": 0, "staple": 1, "plaquette": 2, "plaquette_256": 3,
+           "staple_pairs": 4}
 
 
 class GlasmaError(RuntimeError):
@@ -337,9 +338,9 @@ def glasma_get_info(h):
 
 
 def glasma_set_step_kernel(h, kernel="auto", zlen=0):
-    """Leapfrog step kernel of the context: "auto", "staple", "plaquette"
-    or "plaquette_256"; zlen = z slices per block of the plaquette kernel
-    (0 = automatic)."""
+    """Leapfrog step kernel of the context: "auto", "staple", "plaquette",
+    "plaquette_256" or "staple_pairs" (FP32); zlen = z slices per block of
+    the plaquette kernel (0 = automatic)."""
     _check(load_library().glasma_set_step_kernel(h.ptr, KERNELS[kernel],
                                                  int(zlen)),
            "glasma_set_step_kernel")

@@ -90,21 +90,54 @@ def test_kernel_matches_oracle_on_random_state(G, nc, shape, kernel):
         G.glasma_free(h)
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_fp32_kernels_agree(G, kernel):
-    """FP32 state: each kernel against the FP64 oracle on a random SU(3)
-    state with the 64 x 64 plane.  Bound: per step E and U round at
-    u = 6e-8 relative to O(1) entries, and the four plaquette
+@pytest.mark.parametrize("nc", [2, 3])
+@pytest.mark.parametrize("shape", [(8, 64, 64), (9, 37, 17), (13, 5, 9)])
+@pytest.mark.parametrize("kernel", KERNELS + ["staple_pairs"])
+def test_fp32_kernels_match_oracle(G, nc, shape, kernel):
+    """FP32 state: each kernel against the FP64 oracle on random states; odd
+    nz puts the paired kernel's last lane past the lattice, and its second
+    lane meets the open z boundary on its own.  Bound: per step E and U
+    round at u = 6e-8 relative to O(1) entries, and the four plaquette
     contributions of a link sum a few such roundings; 3 steps stay below
     3 * 8 * u ~ 1.5e-6 of the largest entry."""
-    st = _random_state(3, 8, 64, 64, seed=99)
+    nz, ny, nx = shape
+    st = _random_state(nc, nz, ny, nx, seed=99 + nz)
     ref = O.step(st, 3)
     h = _ctx(G, st, "fp32")
     G.glasma_set_step_kernel(h, kernel)
     G.glasma_step(h, 3)
     U, E, QA, QB, n = G.glasma_get_fields(h)
-    assert rel(U, ref.U) < 1.5e-6 and rel(E, ref.E) < 1.5e-6
-    assert rel(QA, ref.QA) < 1.5e-6 and rel(QB, ref.QB) < 1.5e-6
+    errs = dict(U=rel(U, ref.U), E=rel(E, ref.E), QA=rel(QA, ref.QA),
+                QB=rel(QB, ref.QB))
+    assert all(v < 1.5e-6 for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_paired_kernel_through_a_collision_fp32(G, nc):
+    """The paired staple kernel (the FP32 default) on the ragged 47 x 10 x 12
+    collision (odd nz) through the crossing, against the FP64 oracle at the
+    FP32 bound of the other collision tests, and against the one-site staple
+    kernel at the rounding level of 40 steps."""
+    cfg = dict(gi.small_config(nc, nz=47, sigma_l=2.0), precision="fp32")
+    p = O.Params.from_dict(cfg)
+    rho = gi.mv_rho(cfg["seed"], nc, p.nx, p.ny, p.g2mu)
+    st = O.step(O.init_mv(p, rho), 40)
+    got = {}
+    for kernel in ("staple_pairs", "staple"):
+        h = G.glasma_init_mv(cfg, rho)
+        G.glasma_set_step_kernel(h, kernel)
+        G.glasma_step(h, 40)
+        got[kernel] = G.glasma_get_fields(h)
+        tab, H = G.glasma_tmunu(h)
+        rtab, rH = O.tmunu(st)
+        assert np.max(np.abs(tab[:, 0] - rtab[:, 0])) / np.max(rtab[:, 0]) < 1e-5
+        U, E, QA, QB, n = got[kernel]
+        assert rel(U, st.U) < 3e-5 and rel(E, st.E) < 3e-5
+        assert rel(QA, st.QA) < 3e-5 and rel(QB, st.QB) < 3e-5
+        gmax, grms, rmax = G.glasma_gauss_residual(h)
+        assert gmax < 1e-5 * rmax
+    for a, b in zip(got["staple_pairs"][:4], got["staple"][:4]):
+        assert rel(a, b) < 3e-5
 
 
 def test_su3_64x64_collision_fp64_full_state(G):
@@ -145,6 +178,9 @@ def test_set_step_kernel_rejects_bad_arguments(G):
             G._check(G.load_library().glasma_set_step_kernel(h.ptr, kernel, zlen),
                      "glasma_set_step_kernel")
         assert e.value.code == "INVALID_ARG"
+    # the paired kernel is FP32 only
+    with pytest.raises(G.GlasmaError):
+        G.glasma_set_step_kernel(h, "staple_pairs")
     # rows longer than a block take no plaquette kernel
     wide = G.glasma_init_mv(gi.small_config(2, nz=24, nx=400, ny=2, sigma_l=1.0), None)
     with pytest.raises(G.GlasmaError):
