@@ -289,6 +289,63 @@ typedef struct {
 
 GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
 
+/*
+ * A lattice split into slabs along the beam axis z (Sec. 4: the beam axis
+ * is the long one, 2048 cells against 192^2), one context per rank.  The
+ * leapfrog step (Sec. 3 Eq. lattice_1) couples a link only to the slices
+ * z - 1, z, z + 1, so a slab needs one halo slice from each neighbour,
+ * refreshed before every step; the CPIC hop moves a charge across a slab
+ * boundary along a link whose owner transports it and deposits its current.
+ *
+ * glasma_slab_init: context of the global slices [z0, z1) of the event p
+ *   describes (p->nz is the whole lattice's; rho_host, stream, alloc as for
+ *   glasma_init_mv, every rank passing the same p and charges).  Its local
+ *   lattice is the slab plus a halo slice below (if z0 > 0) and above (if
+ *   z1 < nz); the initial state of every owned and halo slice equals the
+ *   whole lattice's bit for bit.  Leapfrog scheme only.  The step kernel is
+ *   the staple or plaquette kernel (never the site-paired one).  Errors:
+ *   INVALID_ARG (as glasma_init_mv; z0 < 0, z1 > nz, z1 <= z0; implicit
+ *   scheme), OOM, CUDA.
+ * glasma_slab_info: owned global slices [*z0, *z1), local slices, and the
+ *   local indices [*lo, *hi) of the owned slices (any pointer may be NULL).
+ * glasma_slab_set_windows: the charge windows of the whole lattice (first
+ *   global slice and number of slices of nucleus A and B): the union over
+ *   all slabs of the windows glasma_get_info reports after init (global
+ *   slices).  Required once before the first step, so that charges keep
+ *   their co-moving slots when they cross into a neighbour.  Errors:
+ *   INVALID_ARG (not a slab, outside the lattice, not containing the slab's
+ *   own windows), OOM, CUDA.
+ * glasma_slab_message_bytes: bytes of the message sent in direction dir
+ *   (+1: to the rank above, -1: to the rank below).
+ * glasma_slab_pack: write that message into dev_buf (device memory of the
+ *   caller, 16-byte aligned, message_bytes long), asynchronously on the
+ *   context's stream: dir +1 carries the links of all three directions,
+ *   E_z and nucleus B's charge of the top owned slice; dir -1 the
+ *   transverse links and nucleus A's charge of the bottom owned slice.
+ *   Layout: links [direction][complex component][site] as (re, im) reals in
+ *   the stored form (FP32: U - 1), E_z [colour][site], charge
+ *   [colour][site] (zeros outside the nucleus' window).
+ * glasma_slab_unpack: write a received message into the halo: dir -1 a
+ *   message from the rank below (its dir +1 message), dir +1 one from the
+ *   rank above; asynchronous on the context's stream.
+ * Protocol per step: every rank packs its messages, sends them, receives
+ *   its neighbours' and unpacks them, then calls glasma_step(c, 1) (a slab
+ *   context takes one step per exchange).  glasma_tmunu then returns the
+ *   z1 - z0 rows of the owned slices and their partial energy (the whole
+ *   lattice's H is the sum of the gathered rows in z order),
+ *   glasma_gauss_residual the residual over the owned slices, and
+ *   glasma_get_fields the local lattice (charges on owned slices only).
+ *   Errors: INVALID_ARG (bad dir, no neighbour that way, unaligned buffer),
+ *   CUDA.
+ */
+GLASMA_API int glasma_slab_init(const glasma_params* p, const double* rho_host, int z0, int z1, void* stream,
+                                const glasma_allocator* alloc, glasma_ctx** out);
+GLASMA_API int glasma_slab_info(const glasma_ctx* c, int* z0, int* z1, int* nz_local, int* lo, int* hi);
+GLASMA_API int glasma_slab_set_windows(glasma_ctx* c, int zA0, int WA, int zB0, int WB);
+GLASMA_API int glasma_slab_message_bytes(const glasma_ctx* c, int dir, size_t* bytes);
+GLASMA_API int glasma_slab_pack(glasma_ctx* c, int dir, void* dev_buf);
+GLASMA_API int glasma_slab_unpack(glasma_ctx* c, int dir, const void* dev_buf);
+
 /* Kernels of the leapfrog step (the same update, Sec. 3 Eqs. lattice_1,
  * plaquette, lattice_2, continuity, in two work decompositions):
  *   GLASMA_KERNEL_STAPLE       one thread per link; each link sums its four

@@ -141,7 +141,7 @@ bool use_plaq_kernel(const glasma_ctx* c) {
 }
 
 bool use_pair_kernel(const glasma_ctx* c) {
-  if (c->rs != 4) return false;
+  if (c->rs != 4 || c->slab) return false;  // the pairs span the whole z range
   return c->step_kernel == GLASMA_KERNEL_STAPLE_PAIRS || (c->step_kernel == GLASMA_KERNEL_AUTO && c->p.nc == 2);
 }
 
@@ -183,14 +183,31 @@ void glasma_free(glasma_ctx* c) {
   delete c;
 }
 
-int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream, const glasma_allocator* alloc,
-                   glasma_ctx** out) {
+}  // extern "C"
+
+// A context over the global slices [z0, z1) of the lattice p describes,
+// plus one halo slice on each side that has a neighbour (the whole lattice
+// when z0 = 0, z1 = nz).  The context's own lattice is the local one: its
+// params carry the local nz, the open-z rules apply at its ends.
+static int create_ctx(const glasma_params* p, const double* rho_host, void* stream, const glasma_allocator* alloc,
+                      int z0, int z1, glasma_ctx** out) {
   if (!out) return set_error(GLASMA_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   int st = check_params(p);
   if (st) return st;
+  if (z0 < 0 || z1 > p->nz || z1 <= z0) return set_error(GLASMA_ERR_INVALID_ARG, "slab range outside the lattice");
+  const int halo_lo = z0 > 0 ? 1 : 0, halo_hi = z1 < p->nz ? 1 : 0;
+  const int nz_loc = (z1 - z0) + halo_lo + halo_hi;
+  if (nz_loc < 2) return set_error(GLASMA_ERR_INVALID_ARG, "a slab lattice needs at least two slices");
   glasma_ctx* c = new glasma_ctx();
   c->p = *p;
+  c->p.nz = nz_loc;
+  c->slab = !(z0 == 0 && z1 == p->nz);
+  c->zoff = z0 - halo_lo;
+  c->lo = halo_lo;
+  c->hi = halo_lo + (z1 - z0);
+  c->nz_glob = p->nz;
+  p = &c->p;
   cudaGetDevice(&c->device);
   c->stream = (cudaStream_t)stream;
   if (alloc && alloc->alloc && alloc->free) {
@@ -251,19 +268,46 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
   return GLASMA_OK;
 }
 
+extern "C" {
+
+int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream, const glasma_allocator* alloc,
+                   glasma_ctx** out) {
+  if (!p) return set_error(GLASMA_ERR_INVALID_ARG, "params is NULL");
+  return create_ctx(p, rho_host, stream, alloc, 0, p->nz, out);
+}
+
+int glasma_slab_init(const glasma_params* p, const double* rho_host, int z0, int z1, void* stream,
+                     const glasma_allocator* alloc, glasma_ctx** out) {
+  if (!p) return set_error(GLASMA_ERR_INVALID_ARG, "params is NULL");
+  if (p->scheme != GLASMA_LEAPFROG)
+    return set_error(GLASMA_ERR_INVALID_ARG, "slab contexts run the leapfrog scheme");
+  return create_ctx(p, rho_host, stream, alloc, z0, z1, out);
+}
+
 int glasma_step(glasma_ctx* c, int n_steps) {
   if (!c || n_steps < 0) return set_error(GLASMA_ERR_INVALID_ARG, "bad context or n_steps");
+  if (c->slab && !c->slab_windows)
+    return set_error(GLASMA_ERR_INVALID_ARG, "a slab context needs glasma_slab_set_windows before stepping");
+  if (c->slab && n_steps > 1)
+    return set_error(GLASMA_ERR_INVALID_ARG, "a slab context takes one step per halo exchange");
   cudaSetDevice(c->device);
   int launches = 0;
   for (int k = 0; k < n_steps; ++k) {
     const bool hop = hop_at(c->n, c->hop_p, c->hop_q);
     if (hop) {
-      if (c->WB > 0 && c->zB0 + c->WB - 1 >= c->g.nz - 1)
+      // in global slices (a slab's windows are the whole lattice's)
+      if (c->WB > 0 && c->zB0 + c->zoff + c->WB - 1 >= c->nz_glob - 1)
         return set_error(GLASMA_ERR_PARTICLE_EXIT, "nucleus B reached the upper z boundary");
-      if (c->WA > 0 && c->zA0 <= 0)
+      if (c->WA > 0 && c->zA0 + c->zoff <= 0)
         return set_error(GLASMA_ERR_PARTICLE_EXIT, "nucleus A reached the lower z boundary");
     }
     int st;
+    if (hop && c->lo > 0) {
+      // the charge of B on the lower halo slice crosses into the slab
+      st = slab_halo_hop(c);
+      if (st) return st;
+      launches += 1;
+    }
     if (c->p.scheme == GLASMA_IMPLICIT) {
       int iters = 0;
       st = launch_step_implicit(c, hop, &iters);
@@ -309,14 +353,15 @@ int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total) {
   std::vector<double> tab(4 * (size_t)c->g.nz);
   int st = launch_tmunu(c, hop, tab.data());
   if (st) return st;
+  // the owned slices (all of them for a whole lattice)
   double sum = 0.0;
   bool bad = false;
-  for (int iz = 0; iz < c->g.nz; ++iz) {
+  for (int iz = c->lo; iz < c->hi; ++iz) {
     for (int k = 0; k < 4; ++k)
       if (!isfinite(tab[4 * iz + k])) bad = true;
     sum += tab[4 * iz];
   }
-  if (out) memcpy(out, tab.data(), sizeof(double) * tab.size());
+  if (out) memcpy(out, tab.data() + 4 * (size_t)c->lo, sizeof(double) * 4 * (size_t)(c->hi - c->lo));
   if (energy_total) *energy_total = c->p.a_t * c->p.a_t * c->p.a_z * (double)c->g.nxy * sum;
   if (bad) return set_error(GLASMA_ERR_NONFINITE, "T^{mu nu} met a non-finite value");
   return GLASMA_OK;
@@ -469,9 +514,12 @@ int glasma_get_fields(glasma_ctx* c, double* U, double* E, double* QA, double* Q
     st = reals_to_host(c, qd[N], (size_t)na * W[N] * nxy, raw);
     if (st) return st;
     for (int a = 0; a < na; ++a)
-      for (int w = 0; w < W[N]; ++w)
+      for (int w = 0; w < W[N]; ++w) {
+        const int iz = z0[N] + w;  // a slab's windows reach past its slices
+        if (iz < c->lo || iz >= c->hi) continue;
         for (int64_t t = 0; t < nxy; ++t)
-          qh[N][((size_t)(z0[N] + w) * nxy + t) * na + a] = raw[((size_t)a * W[N] + w) * nxy + t];
+          qh[N][((size_t)iz * nxy + t) * na + a] = raw[((size_t)a * W[N] + w) * nxy + t];
+      }
   }
   if (step_n) *step_n = c->n;
   return GLASMA_OK;
@@ -519,6 +567,7 @@ static void support(const glasma_ctx* c, const double* Q, int* lo, int* W) {
 int glasma_set_fields(glasma_ctx* c, const double* U, const double* E, const double* QA, const double* QB,
                       const double* U_prev, long long step_n) {
   if (!c || !U || !E || step_n < 0) return set_error(GLASMA_ERR_INVALID_ARG, "bad context, U, E or step_n");
+  if (c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "set_fields takes a whole lattice, not a slab");
   cudaSetDevice(c->device);
   const int64_t V = c->g.V, nxy = c->g.nxy;
   const int na = c->na, nc = c->p.nc;
@@ -625,6 +674,7 @@ int glasma_state_bytes(const glasma_ctx* c, size_t* bytes) {
 }
 
 int glasma_get_state(glasma_ctx* c, void* host_buf, size_t bytes) {
+  if (c && c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "checkpoints hold whole lattices, not slabs");
   size_t need;
   int st = glasma_state_bytes(c, &need);
   if (st) return st;
@@ -672,6 +722,7 @@ int glasma_get_state(glasma_ctx* c, void* host_buf, size_t bytes) {
 
 int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes) {
   if (!c || !host_buf || bytes < sizeof(StateHeader)) return set_error(GLASMA_ERR_INVALID_ARG, "bad state buffer");
+  if (c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "checkpoints hold whole lattices, not slabs");
   cudaSetDevice(c->device);
   StateHeader h;
   memcpy(&h, host_buf, sizeof(h));
@@ -745,8 +796,8 @@ int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen) {
   if (kernel != GLASMA_KERNEL_AUTO && kernel != GLASMA_KERNEL_STAPLE && kernel != GLASMA_KERNEL_PLAQUETTE &&
       kernel != GLASMA_KERNEL_PLAQUETTE_256 && kernel != GLASMA_KERNEL_STAPLE_PAIRS)
     return set_error(GLASMA_ERR_INVALID_ARG, "unknown step kernel");
-  if (kernel == GLASMA_KERNEL_STAPLE_PAIRS && c->rs != 4)
-    return set_error(GLASMA_ERR_INVALID_ARG, "the paired staple kernel needs FP32 state");
+  if (kernel == GLASMA_KERNEL_STAPLE_PAIRS && (c->rs != 4 || c->slab))
+    return set_error(GLASMA_ERR_INVALID_ARG, "the paired staple kernel needs FP32 state of a whole lattice");
   if (zlen < 0 || zlen > c->g.nz) return set_error(GLASMA_ERR_INVALID_ARG, "zlen must be in [0, nz]");
   const int old = c->step_kernel;
   c->step_kernel = kernel;
@@ -758,6 +809,82 @@ int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen) {
   return GLASMA_OK;
 }
 
+int glasma_slab_info(const glasma_ctx* c, int* z0, int* z1, int* nz_local, int* lo, int* hi) {
+  if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
+  if (z0) *z0 = c->zoff + c->lo;
+  if (z1) *z1 = c->zoff + c->hi;
+  if (nz_local) *nz_local = c->g.nz;
+  if (lo) *lo = c->lo;
+  if (hi) *hi = c->hi;
+  return GLASMA_OK;
+}
+
+int glasma_slab_set_windows(glasma_ctx* c, int zA0, int WA, int zB0, int WB) {
+  if (!c || !c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "not a slab context");
+  if (WA < 0 || WB < 0 || zA0 < 0 || zB0 < 0 || zA0 + WA > c->nz_glob || zB0 + WB > c->nz_glob)
+    return set_error(GLASMA_ERR_INVALID_ARG, "window outside the lattice");
+  cudaSetDevice(c->device);
+  const int na = c->na;
+  const int64_t nxy = c->g.nxy;
+  // the new windows (global slices) must hold the slab's own charges
+  const int old0[2] = {c->zA0 + c->zoff, c->zB0 + c->zoff}, oldW[2] = {c->WA, c->WB};
+  const int new0[2] = {zA0, zB0}, newW[2] = {WA, WB};
+  for (int N = 0; N < 2; ++N)
+    if (oldW[N] > 0 && (old0[N] < new0[N] || old0[N] + oldW[N] > new0[N] + newW[N]))
+      return set_error(GLASMA_ERR_INVALID_ARG, "the windows must contain the slab's own charge windows");
+  void** q[2] = {&c->QA, &c->QB};
+  size_t* cap[2] = {&c->QA_cap, &c->QB_cap};
+  for (int N = 0; N < 2; ++N) {
+    const size_t w = (size_t)(newW[N] > 0 ? newW[N] : 1);
+    void* nq = ctx_alloc(c, c->rs * na * w * nxy);
+    if (!nq) return set_error(GLASMA_ERR_OOM, "charge window allocation failed");
+    int st = cuda_check(cudaMemsetAsync(nq, 0, c->rs * na * w * nxy, c->stream), "window clear");
+    for (int a = 0; a < na && !st && oldW[N] > 0; ++a) {
+      const size_t row = c->rs * (size_t)nxy;
+      char* dst = (char*)nq + ((size_t)a * newW[N] + (old0[N] - new0[N])) * row;
+      const char* src = (const char*)*q[N] + (size_t)a * oldW[N] * row;
+      st = cuda_check(cudaMemcpyAsync(dst, src, row * oldW[N], cudaMemcpyDeviceToDevice, c->stream), "window copy");
+    }
+    if (st) {
+      ctx_free(c, nq);
+      return st;
+    }
+    ctx_free(c, *q[N]);
+    *q[N] = nq;
+    *cap[N] = w;
+  }
+  c->zA0 = zA0 - c->zoff;
+  c->WA = WA;
+  c->zB0 = zB0 - c->zoff;
+  c->WB = WB;
+  c->slab_windows = true;
+  return cuda_check(cudaStreamSynchronize(c->stream), "window sync");
+}
+
+int glasma_slab_message_bytes(const glasma_ctx* c, int dir, size_t* bytes) {
+  if (!c || !bytes || (dir != 1 && dir != -1)) return set_error(GLASMA_ERR_INVALID_ARG, "bad context, dir or bytes");
+  *bytes = c->rs * slab_msg_elems(c, dir);
+  return GLASMA_OK;
+}
+
+int glasma_slab_pack(glasma_ctx* c, int dir, void* dev_buf) {
+  if (!c || !dev_buf || (dir != 1 && dir != -1)) return set_error(GLASMA_ERR_INVALID_ARG, "bad context, dir or buffer");
+  if ((dir == 1 && c->hi == c->g.nz) || (dir == -1 && c->lo == 0))
+    return set_error(GLASMA_ERR_INVALID_ARG, "no neighbouring slab in that direction");
+  if (((uintptr_t)dev_buf & 15) != 0) return set_error(GLASMA_ERR_INVALID_ARG, "message buffer must be 16-byte aligned");
+  cudaSetDevice(c->device);
+  return slab_pack(c, dir, dev_buf);
+}
+
+int glasma_slab_unpack(glasma_ctx* c, int dir, const void* dev_buf) {
+  if (!c || !dev_buf || (dir != 1 && dir != -1)) return set_error(GLASMA_ERR_INVALID_ARG, "bad context, dir or buffer");
+  if ((dir == 1 && c->hi == c->g.nz) || (dir == -1 && c->lo == 0))
+    return set_error(GLASMA_ERR_INVALID_ARG, "no neighbouring slab in that direction");
+  if (((uintptr_t)dev_buf & 15) != 0) return set_error(GLASMA_ERR_INVALID_ARG, "message buffer must be 16-byte aligned");
+  cudaSetDevice(c->device);
+  return slab_unpack(c, dir, dev_buf);
+}
+
 int glasma_get_info(const glasma_ctx* c, glasma_info* info) {
   if (!c || !info) return set_error(GLASMA_ERR_INVALID_ARG, "bad context or info");
   info->sites = (long long)c->g.V;
@@ -765,9 +892,9 @@ int glasma_get_info(const glasma_ctx* c, glasma_info* info) {
   info->nc = c->p.nc;
   info->precision = c->p.precision;
   info->scheme = c->p.scheme;
-  info->window_a[0] = c->zA0;
+  info->window_a[0] = c->zA0 + c->zoff;  // global slices
   info->window_a[1] = c->WA;
-  info->window_b[0] = c->zB0;
+  info->window_b[0] = c->zB0 + c->zoff;
   info->window_b[1] = c->WB;
   info->state_device_bytes = 2 * link_bytes(c) + c->rs * 3 * (size_t)c->na * c->g.V +
                              c->rs * (size_t)c->na * (c->QA_cap + c->QB_cap) * c->g.nxy;

@@ -43,6 +43,13 @@ struct glasma_ctx {
   int step_kernel = 0;        // GLASMA_KERNEL_* of the leapfrog step
   int step_zlen = 0;          // z slices per block of the plaquette kernel (0 = automatic)
   bool plaq_ready = false;    // the plaquette kernel's attributes are set on this device
+  // z slab of a lattice split along the beam axis (glasma_slab_init): the
+  // context's lattice is the slab with its halo slices; local slice 0 is
+  // global slice zoff; the owned slices are [lo, hi), the others halos.  An
+  // ordinary context has zoff = 0, lo = 0, hi = nz, nz_glob = nz.
+  bool slab = false;
+  bool slab_windows = false;  // the windows hold the whole lattice's extent
+  int zoff = 0, lo = 0, hi = 0, nz_glob = 0;
   struct Alloc {
     void* ptr;
     size_t bytes;
@@ -89,7 +96,12 @@ int plaq_default_zlen(const glasma_ctx* c);
 // any capture of its launches)
 int plaq_prepare(glasma_ctx* c);
 int launch_step_implicit(glasma_ctx* c, bool hop, int* iters);
-int launch_gauss(glasma_ctx* c, double* out3);
+int launch_gauss(glasma_ctx* c, double* out3);  // over the owned slices [lo, hi)
+// slab halo messages (k_slab.cu)
+size_t slab_msg_elems(const glasma_ctx* c, int dir);
+int slab_pack(glasma_ctx* c, int dir, void* buf);
+int slab_unpack(glasma_ctx* c, int dir, const void* buf);
+int slab_halo_hop(glasma_ctx* c);
 // host_tab != NULL: read the table back and synchronise; dev_tab != NULL:
 // write the table there instead of the context's own buffer
 int launch_tmunu(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab = nullptr);

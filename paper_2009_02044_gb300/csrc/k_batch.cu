@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(3 * BX, sizeof(R) == 4 ? BatchOcc<BX>::blocks 
   a.WA = ev.WA;
   a.zB0 = ev.zB0;
   a.WB = ev.WB;
+  a.zlo = 0;
   step_link<NC, R>(a, (int)threadIdx.y, tile * BX + threadIdx.x, iz);
 }
 
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(3 * BX, sizeof(R) == 4 ? PersistOcc<BX>::block
       s.WA = ev.WA;
       s.zB0 = ev.zB0 + moved;
       s.WB = ev.WB;
+      s.zlo = 0;
       step_link<NC, R>(s, (int)threadIdx.y, (local % ev.ntb) * BX + threadIdx.x, (int)(local / ev.ntb));
     }
     if (k + 1 < a.steps &&
@@ -517,6 +519,7 @@ GLASMA_API int glasma_batch_create(glasma_ctx* const* ctxs, int n, glasma_batch*
     const glasma_ctx* c = ctxs[e];
     if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "NULL context in batch");
     if (c->p.scheme != GLASMA_LEAPFROG) return set_error(GLASMA_ERR_INVALID_ARG, "batched events use the leapfrog scheme");
+    if (c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "batched events are whole lattices, not slabs");
     if (c->p.nc != c0->p.nc || c->p.precision != c0->p.precision || c->p.dt != c0->p.dt || c->p.a_t != c0->p.a_t ||
         c->p.a_z != c0->p.a_z || c->device != c0->device || c->stream != c0->stream)
       return set_error(GLASMA_ERR_INVALID_ARG, "batched events must share nc, precision, dt, a_t, a_z, device and stream");

@@ -83,11 +83,13 @@ __global__ void k_cplx_real_scaled(const double2* in, double* out, int64_t total
 }
 
 // lam[(t*2 + N)*nz + iz], t = 0: t0, 1: t0 - dt; N = 0: A, 1: B
-__global__ void k_profile(double* lam, int nz, double a_z, double sigma, double zA0, double zB0, double dt) {
+// (iz is local: the slice's global index is iz + zoff)
+__global__ void k_profile(double* lam, int nz, int zoff, double a_z, double sigma, double zA0, double zB0,
+                          double dt) {
   const double erf4 = erf(2.0 * 1.4142135623730950488);  // erf(4 / sqrt 2)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * nz; i += gridDim.x * blockDim.x) {
     const int iz = i % nz, tn = i / nz, N = tn % 2, t = tn / 2;
-    const double z = iz * a_z;
+    const double z = (iz + zoff) * a_z;
     const double zn = N == 0 ? zA0 + (t ? dt : 0.0) : zB0 - (t ? dt : 0.0);
     const double u = (z - zn) / sigma;
     const double uc = fmin(fmax(u, -4.0), 4.0);
@@ -327,10 +329,11 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
   k_dft<<<grid_for(F * nxy), 256, 0, c->stream>>>(w0, w1, F, p.ny, p.nx, 1, +1);
   k_dft<<<grid_for(F * nxy), 256, 0, c->stream>>>(w1, w0, F, p.ny, p.nx, 0, +1);
   k_cplx_real_scaled<<<grid_for(F * nxy), 256, 0, c->stream>>>(w0, rho, F * nxy, 1.0 / (double)nxy);  // rho <- phi
-  // nucleus centres at t0 (box centre +- d)
-  const double zc = p.nz * p.a_z / 2.0;
+  // nucleus centres at t0 (box centre +- d) in global z (a slab's local
+  // slice 0 is global slice zoff)
+  const double zc = c->nz_glob * p.a_z / 2.0;
   const double d = p.z_offset > 0 ? p.z_offset : (ceil(4.0 * p.sigma_l / p.a_z) + 2.0) * p.a_z;
-  k_profile<<<grid_for(4 * p.nz), 256, 0, c->stream>>>(lam, p.nz, p.a_z, p.sigma_l, zc + d, zc - d, p.dt);
+  k_profile<<<grid_for(4 * p.nz), 256, 0, c->stream>>>(lam, p.nz, c->zoff, p.a_z, p.sigma_l, zc + d, zc - d, p.dt);
   cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream);
   typedef typename Group<NC, double>::M MD;
   MD* full = nullptr;
@@ -357,11 +360,13 @@ static int init_t(glasma_ctx* c, const double* rho_host) {
   if (st) return st;
   if (hflag) return set_error(GLASMA_ERR_INVALID_ARG, "init: link change per step too large for the group log");
   // windows: A on slices above the centre, B below; none at the centre
+  // (only the owned slices: a slab's halo slices carry no charge of their
+  // own, and the divergence of its lower halo lacks the slice below)
   int alo = -1, ahi = -1, blo = -1, bhi = -1;
-  for (int iz = 0; iz < p.nz; ++iz) {
+  for (int iz = c->lo; iz < c->hi; ++iz) {
     if (!(hmax[iz] == hmax[iz])) return set_error(GLASMA_ERR_NONFINITE, "init: non-finite charge density");
     if (hmax[iz] == 0.0) continue;
-    const double z = iz * p.a_z;
+    const double z = (iz + c->zoff) * p.a_z;
     if (z > zc) {
       if (alo < 0) alo = iz;
       ahi = iz;
@@ -433,7 +438,7 @@ int device_poisson(const glasma_params& p, const double* in, double* out, int F,
 int device_profile(const glasma_params& p, double* lam, cudaStream_t s) {
   const double zc = p.nz * p.a_z / 2.0;
   const double d = p.z_offset > 0 ? p.z_offset : (ceil(4.0 * p.sigma_l / p.a_z) + 2.0) * p.a_z;
-  k_profile<<<grid_for(4 * p.nz), 256, 0, s>>>(lam, p.nz, p.a_z, p.sigma_l, zc + d, zc - d, p.dt);
+  k_profile<<<grid_for(4 * p.nz), 256, 0, s>>>(lam, p.nz, 0, p.a_z, p.sigma_l, zc + d, zc - d, p.dt);
   return cuda_check(cudaGetLastError(), "profile");
 }
 

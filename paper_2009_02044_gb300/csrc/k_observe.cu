@@ -39,7 +39,8 @@ struct GaussArgs {
   Geom g;
   double ia2[3];  // 1 / a_i^2
   int zA0, WA, zB0, WB;
-  double* part;  // [gridDim][4]
+  int64_t s0, s1;  // sites of the owned slices
+  double* part;    // [gridDim][4]
 };
 
 template <int NC, typename R>
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gauss(GaussArgs<R> a) {
   constexpr int NA = G::NA;
   __shared__ double sh[4][kRedThreads];
   double gmax = 0, gsum2 = 0, rmax = 0, bad = 0;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.g.V;
+  for (int64_t s = a.s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.s1;
        s += (int64_t)gridDim.x * blockDim.x) {
     SiteNbr n = site_nbr(a.g, s);
     double gv[NA];
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kRedThreads) k_fold(const double* part, int nb
 static int reduction_grid(glasma_ctx* c) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  int64_t need = (c->g.V + kRedThreads - 1) / kRedThreads;
+  int64_t need = ((int64_t)(c->hi - c->lo) * c->g.nxy + kRedThreads - 1) / kRedThreads;
   int64_t nb = (int64_t)sms * 4;
   return (int)(need < nb ? need : nb);
 }
@@ -138,6 +139,8 @@ static int gauss_t(glasma_ctx* c, double* out3) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
+  a.s0 = (int64_t)c->lo * c->g.nxy;
+  a.s1 = (int64_t)c->hi * c->g.nxy;
   const int nb = reduction_grid(c);
   // partials, then the op table and the 4 results, in the context's scratch
   if ((size_t)nb * 4 + 8 > c->red_cap) return set_error(GLASMA_ERR_INTERNAL, "reduction scratch too small");
@@ -155,7 +158,7 @@ static int gauss_t(glasma_ctx* c, double* out3) {
   st = cuda_check(cudaStreamSynchronize(c->stream), "gauss sync");
   if (st) return st;
   out3[0] = h[0];
-  out3[1] = sqrt(h[1] / ((double)c->g.V * (c->na)));
+  out3[1] = sqrt(h[1] / ((double)(a.s1 - a.s0) * (c->na)));
   out3[2] = h[2];
   if (h[3] != 0.0) return set_error(GLASMA_ERR_NONFINITE, "Gauss residual met a non-finite value");
   return GLASMA_OK;

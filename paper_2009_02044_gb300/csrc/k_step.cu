@@ -17,7 +17,7 @@ template <> struct StepOcc<double> { static constexpr int blocks = 1; };
 
 template <int NC, typename R>
 __global__ void __launch_bounds__(192, StepOcc<R>::blocks) k_step_leapfrog(StepArgs<R> a) {
-  step_link<NC, R>(a, (int)threadIdx.y, blockIdx.x * blockDim.x + threadIdx.x, (int)blockIdx.y);
+  step_link<NC, R>(a, (int)threadIdx.y, blockIdx.x * blockDim.x + threadIdx.x, (int)blockIdx.y + a.zlo);
 }
 
 template <int NC, typename R>
@@ -39,9 +39,10 @@ static int launch_t(glasma_ctx* c, bool hop) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
+  a.zlo = c->lo;
   const int bs = 64;
   const unsigned ntb = (unsigned)((c->g.nxy + bs - 1) / bs);
-  k_step_leapfrog<NC, R><<<dim3(ntb, (unsigned)c->g.nz), dim3(bs, 3), 0, c->stream>>>(a);
+  k_step_leapfrog<NC, R><<<dim3(ntb, (unsigned)(c->hi - c->lo)), dim3(bs, 3), 0, c->stream>>>(a);
   return cuda_check(cudaGetLastError(), "k_step_leapfrog launch");
 }
 
@@ -73,6 +74,8 @@ static int launch_pair_t(glasma_ctx* c, bool hop) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
+  a.zlo = 0;
+  if (c->slab) return set_error(GLASMA_ERR_INTERNAL, "the paired step kernel does not take slab contexts");
   const int bs = 64;
   const int H = (c->g.nz + 1) / 2;
   const unsigned ntb = (unsigned)((c->g.nxy + bs - 1) / bs);

@@ -45,6 +45,7 @@ struct PlaqArgs {
   int rows;      // interior rows per block (== ny: the block holds the plane)
   int halo;      // 1 if the block has a -y halo row
   int zlen;      // slices per block
+  int zhi;       // one past the last slice updated (s.zlo is the first)
 };
 
 // shared-memory vectors per site: the +x contributions to the y and z
@@ -111,35 +112,26 @@ __global__ void __launch_bounds__(PlaqOcc<R, V>::threads, PlaqOcc<R, V>::blocks)
   const int slot_my = pa.halo ? l - nx : (r == 0 ? l + (ny - 1) * nx : l - nx);
   const R wt = a.w[0], wz = a.w[2];
 
-  const int z0 = blockIdx.y * pa.zlen;
-  const int z1 = min(z0 + pa.zlen, g.nz);
+  const int z0 = a.zlo + blockIdx.y * pa.zlen;
+  const int z1 = min(z0 + pa.zlen, pa.zhi);
   R* cz = sm;
-  if (inner) {
-    R p[NA];
-    if (z0 > 0) {
-      // warm-up: pBA of the (x, z) and (y, z) plaquettes of slice z0 - 1
-      const int64_t s = (int64_t)(z0 - 1) * g.nxy + t;
-      M A, B;
-      W::partials(a.U, g, 0, 2, s, s - t + txp, s + g.nxy, A, B);
-      LinkAlg<NC, R>::proj_prod(B, A, p);
+  if (inner && z0 == 0) {
 #pragma unroll
-      for (int c = 0; c < NA; ++c) cz[(kCzX * NA + c) * TS + l] = wz * p[c];
-      W::partials(a.U, g, 1, 2, s, s - t + typ, s + g.nxy, A, B);
-      LinkAlg<NC, R>::proj_prod(B, A, p);
-#pragma unroll
-      for (int c = 0; c < NA; ++c) cz[(kCzY * NA + c) * TS + l] = wz * p[c];
-    } else {
-#pragma unroll
-      for (int c = 0; c < NA; ++c) cz[(kCzX * NA + c) * TS + l] = cz[(kCzY * NA + c) * TS + l] = R(0);
-    }
+    for (int c = 0; c < NA; ++c) cz[(kCzX * NA + c) * TS + l] = cz[(kCzY * NA + c) * TS + l] = R(0);
   }
 
-  for (int iz = z0; iz < z1; ++iz) {
+  // A chunk that starts above slice 0 first runs a warm-up iteration on the
+  // slice below it, which only forms the +z contributions (pBA of the
+  // (x, z) and (y, z) plaquettes) of that slice: the same instructions as
+  // in every other iteration, so the result does not depend on where the
+  // chunks (or the slabs of a split lattice) begin.
+  for (int iz = z0 > 0 ? z0 - 1 : z0; iz < z1; ++iz) {
+    const bool warm = iz < z0;
     R* buf = sm;
     const int64_t s = (int64_t)iz * g.nxy + t;
     const int64_t sxp = s - t + txp, syp = s - t + typ;
     const bool zlink = iz < g.nz - 1;
-    if (inner) {
+    if (inner && !warm) {
       // force partials start from the +z contributions of slice iz - 1
 #pragma unroll
       for (int c = 0; c < NA; ++c) {
@@ -149,14 +141,16 @@ __global__ void __launch_bounds__(PlaqOcc<R, V>::threads, PlaqOcc<R, V>::blocks)
       }
     }
     // planes (x, y), (x, z), (y, z); the last slice has only (x, y), the
-    // halo row needs pBA of (x, y) and pAB of (y, z) only
+    // halo row needs pBA of (x, y) and pAB of (y, z) only, the warm-up
+    // pBA of (x, z) and (y, z) only
     const int np = zlink ? 3 : 1;
 #pragma unroll 1
-    for (int pl = 0; pl < np; ++pl) {
+    for (int pl = warm ? 1 : 0; pl < np; ++pl) {
       const int pa_ = pl == 2 ? 1 : 0, pb = pl == 0 ? 1 : 2;
       // threads of rows past the lattice's last row (a ragged last block)
       // and past the block's rows do nothing
-      const bool need_ab = inner || (hrow && pl == 2), need_ba = inner || (hrow && pl == 0);
+      const bool need_ab = !warm && (inner || (hrow && pl == 2));
+      const bool need_ba = inner || (!warm && hrow && pl == 0);
       if (!(need_ab || need_ba)) continue;
       const int64_t sa = pa_ == 0 ? sxp : syp, sb = pb == 1 ? syp : s + g.nxy;
       const R wa = wt, wb = pb == 2 ? wz : wt;  // w_a, w_b = 2 / a^2 of the plane's directions
@@ -176,7 +170,7 @@ __global__ void __launch_bounds__(PlaqOcc<R, V>::threads, PlaqOcc<R, V>::blocks)
 #pragma unroll
         for (int c = 0; c < NA; ++c) buf[(vba * NA + c) * TS + l] = wb * p[c];
       }
-      if (inner) {
+      if (inner && !warm) {
         W::corner0(a.U, g, pa_, pb, s, A, p);
         R* fa = buf + (kF + pa_) * NA * TS + l;
         R* fb = buf + (kF + pb) * NA * TS + l;
@@ -187,6 +181,7 @@ __global__ void __launch_bounds__(PlaqOcc<R, V>::threads, PlaqOcc<R, V>::blocks)
         }
       }
     }
+    if (warm) continue;  // the same for every thread of the block: no barrier is skipped unevenly
     __syncthreads();
     if (inner) {
 #pragma unroll
@@ -260,6 +255,8 @@ static int launch_plaq_t(glasma_ctx* c, bool hop, int zlen) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
+  a.zlo = c->lo;
+  pa.zhi = c->hi;
   constexpr int T = PlaqOcc<R, V>::threads;
   if (!plaq_shape(c->g.nx, c->g.ny, T, &pa.rows, &pa.halo))
     return set_error(GLASMA_ERR_INTERNAL, "plaquette kernel: transverse rows too long");
@@ -271,7 +268,7 @@ static int launch_plaq_t(glasma_ctx* c, bool hop, int zlen) {
     if (st) return st;
   }
   const unsigned tiles = (unsigned)((c->g.ny + pa.rows - 1) / pa.rows);
-  const unsigned chunks = (unsigned)((c->g.nz + zlen - 1) / zlen);
+  const unsigned chunks = (unsigned)((c->hi - c->lo + zlen - 1) / zlen);
   const unsigned threads = (unsigned)((TS + 31) / 32 * 32);
   k_step_plaq<NC, R, V><<<dim3(tiles, chunks), threads, smem, c->stream>>>(pa);
   return cuda_check(cudaGetLastError(), "k_step_plaq launch");
@@ -316,7 +313,7 @@ int plaq_default_zlen(const glasma_ctx* c) {
   if (!plaq_shape(c->g.nx, c->g.ny, T, &rows, &halo)) return 16;
   const long long tiles = (c->g.ny + rows - 1) / rows;
   const long long slots = 152LL * (c->rs == 8 ? 1 : 2);
-  long long z = tiles * c->g.nz / (8 * slots);
+  long long z = tiles * (c->hi - c->lo) / (8 * slots);
   if (z < 4) z = 4;
   if (z > 64) z = 64;
   return (int)z;

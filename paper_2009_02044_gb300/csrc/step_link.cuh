@@ -19,6 +19,7 @@ struct StepArgs {
   R az2;    // a_z^2
   int hop;
   int zA0, WA, zB0, WB;
+  int zlo;  // first slice the launch updates (the grid covers the owned slices)
 };
 
 // Steps (1)-(3) below for link i of the site s = iz*nxy + t, given the

@@ -95,6 +95,16 @@ def load_library(path=LIB_PATH):
         "glasma_set_state": (C.c_int, [P, P, C.c_size_t]),
         "glasma_get_info": (C.c_int, [P, C.POINTER(glasma_info)]),
         "glasma_set_step_kernel": (C.c_int, [P, C.c_int, C.c_int]),
+        "glasma_slab_init": (C.c_int, [C.POINTER(glasma_params), dp, C.c_int,
+                                       C.c_int, P, C.POINTER(glasma_allocator),
+                                       C.POINTER(C.c_void_p)]),
+        "glasma_slab_info": (C.c_int, [P] + [C.POINTER(C.c_int)] * 5),
+        "glasma_slab_set_windows": (C.c_int, [P, C.c_int, C.c_int, C.c_int,
+                                              C.c_int]),
+        "glasma_slab_message_bytes": (C.c_int, [P, C.c_int,
+                                                C.POINTER(C.c_size_t)]),
+        "glasma_slab_pack": (C.c_int, [P, C.c_int, P]),
+        "glasma_slab_unpack": (C.c_int, [P, C.c_int, P]),
         "glasma_gauss_residual_static": (
             C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                       C.c_double, C.c_double, P, P, P, C.c_int, C.c_int, P,
@@ -206,6 +216,17 @@ def glasma_init_mv(cfg, rho=None, stream=None, torch_memory=True):
     rho: None (draw from cfg['seed'] on the device) or float64 array
     [2][nc^2-1][ny][nx].  stream: a torch.cuda.Stream, a raw cudaStream_t
     integer or None (torch's current stream)."""
+    return _create(cfg, rho, stream, torch_memory, None)
+
+
+def glasma_slab_init(cfg, z0, z1, rho=None, stream=None, torch_memory=True):
+    """Context of the global slices [z0, z1) of the event cfg describes,
+    with its halo slices (see include/glasma.h); the handle's `slab` holds
+    (z0, z1, local slices, lo, hi)."""
+    return _create(cfg, rho, stream, torch_memory, (int(z0), int(z1)))
+
+
+def _create(cfg, rho, stream, torch_memory, slab):
     lib = load_library()
     p = make_params(cfg)
     if rho is not None:
@@ -227,10 +248,20 @@ def glasma_init_mv(cfg, rho=None, stream=None, torch_memory=True):
         keep = (a, keep)
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     out = C.c_void_p()
-    st = lib.glasma_init_mv(C.byref(p), _dptr(rho), C.c_void_p(s or 0),
-                            alloc_ptr, C.byref(out))
-    _check(st, "glasma_init_mv")
-    return Handle(out, p, keep)
+    if slab is None:
+        st = lib.glasma_init_mv(C.byref(p), _dptr(rho), C.c_void_p(s or 0),
+                                alloc_ptr, C.byref(out))
+        _check(st, "glasma_init_mv")
+        return Handle(out, p, keep)
+    st = lib.glasma_slab_init(C.byref(p), _dptr(rho), slab[0], slab[1],
+                              C.c_void_p(s or 0), alloc_ptr, C.byref(out))
+    _check(st, "glasma_slab_init")
+    h = Handle(out, p, keep)
+    v = [C.c_int() for _ in range(5)]
+    _check(lib.glasma_slab_info(out, *[C.byref(x) for x in v]),
+           "glasma_slab_info")
+    h.slab = tuple(x.value for x in v)
+    return h
 
 
 class Handle:
@@ -240,6 +271,17 @@ class Handle:
         self.ptr = ptr
         self.params = params
         self._keep = keep
+        self.slab = None      # (z0, z1, local slices, lo, hi) of a slab
+
+    @property
+    def local_nz(self):
+        """Slices of the context's own lattice (a slab's with its halos)."""
+        return self.params.nz if self.slab is None else self.slab[2]
+
+    @property
+    def rows(self):
+        """T^{mu nu} rows glasma_tmunu returns (the owned slices)."""
+        return self.params.nz if self.slab is None else self.slab[1] - self.slab[0]
 
     @property
     def na(self):
@@ -270,7 +312,7 @@ def glasma_gauss_residual(h):
 
 
 def glasma_tmunu(h):
-    tab = np.empty((h.params.nz, 4))
+    tab = np.empty((h.rows, 4))
     H = C.c_double()
     _check(load_library().glasma_tmunu(h.ptr, _dptr(tab), C.byref(H)),
            "glasma_tmunu")
@@ -279,12 +321,13 @@ def glasma_tmunu(h):
 
 def glasma_get_fields(h):
     p = h.params
-    V = p.nz * p.ny * p.nx
+    nz = h.local_nz
+    V = nz * p.ny * p.nx
     na, nc = h.na, p.nc
-    U = np.empty((3, p.nz, p.ny, p.nx, nc, nc, 2))
-    E = np.empty((3, p.nz, p.ny, p.nx, na))
-    QA = np.empty((p.nz, p.ny, p.nx, na))
-    QB = np.empty((p.nz, p.ny, p.nx, na))
+    U = np.empty((3, nz, p.ny, p.nx, nc, nc, 2))
+    E = np.empty((3, nz, p.ny, p.nx, na))
+    QA = np.empty((nz, p.ny, p.nx, na))
+    QB = np.empty((nz, p.ny, p.nx, na))
     n = C.c_longlong()
     _check(load_library().glasma_get_fields(h.ptr, _dptr(U), _dptr(E),
                                             _dptr(QA), _dptr(QB), C.byref(n)),
@@ -344,6 +387,33 @@ def glasma_set_step_kernel(h, kernel="auto", zlen=0):
     _check(load_library().glasma_set_step_kernel(h.ptr, KERNELS[kernel],
                                                  int(zlen)),
            "glasma_set_step_kernel")
+
+
+def glasma_slab_set_windows(h, window_a, window_b):
+    """Whole-lattice charge windows (first global slice, slices) of A, B."""
+    _check(load_library().glasma_slab_set_windows(
+        h.ptr, int(window_a[0]), int(window_a[1]), int(window_b[0]),
+        int(window_b[1])), "glasma_slab_set_windows")
+
+
+def glasma_slab_message_bytes(h, direction):
+    n = C.c_size_t()
+    _check(load_library().glasma_slab_message_bytes(h.ptr, int(direction),
+                                                    C.byref(n)),
+           "glasma_slab_message_bytes")
+    return n.value
+
+
+def glasma_slab_pack(h, direction, dev_ptr):
+    _check(load_library().glasma_slab_pack(h.ptr, int(direction),
+                                           C.c_void_p(dev_ptr)),
+           "glasma_slab_pack")
+
+
+def glasma_slab_unpack(h, direction, dev_ptr):
+    _check(load_library().glasma_slab_unpack(h.ptr, int(direction),
+                                             C.c_void_p(dev_ptr)),
+           "glasma_slab_unpack")
 
 
 def glasma_free(h):

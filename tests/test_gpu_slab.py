@@ -1,0 +1,107 @@
+"""Slab contexts on one GPU (glasma_slab_*), exchanging their halo slices by
+device copies (paper_2009_02044_gb300.slab.LocalTransport), against one
+context of the whole lattice, bit for bit: the links, fields and charges of
+every owned slice, the T^{mu nu}(z) rows, the total energy summed in z
+order, and the Gauss residual maximum, through the collision.  The oracle
+side of the same decomposition is tests/test_oracle_slab.py."""
+import numpy as np
+import pytest
+
+import glasma_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_02044_gb300 import build as B
+    B.build()
+    from paper_2009_02044_gb300 import glasma
+    glasma.load_library()
+    return glasma
+
+
+def _run(G, cfg, nranks, steps, kernel):
+    from paper_2009_02044_gb300 import slab as SL
+    whole = G.glasma_init_mv(cfg, None)
+    G.glasma_set_step_kernel(whole, kernel)
+    ranks = [SL.SlabRank(cfg, r, nranks) for r in range(nranks)]
+    for r in ranks:
+        G.glasma_set_step_kernel(r.h, kernel)
+    T = SL.LocalTransport(ranks)
+    T.setup()
+    for k in range(steps):
+        T.step()
+        G.glasma_step(whole, 1)
+    T.exchange()                       # fresh halos for the observables
+    return whole, ranks, T
+
+
+def _compare(G, cfg, whole, ranks, T):
+    from paper_2009_02044_gb300 import slab as SL
+    U, E, QA, QB, n = G.glasma_get_fields(whole)
+    for r in ranks:
+        Ur, Er, QAr, QBr, nr = G.glasma_get_fields(r.h)
+        z0, z1, nzl, lo, hi = r.h.slab
+        assert nr == n
+        assert np.array_equal(Ur[:, lo:hi], U[:, z0:z1]), (r.rank, "U")
+        assert np.array_equal(Er[:, lo:hi], E[:, z0:z1]), (r.rank, "E")
+        assert np.array_equal(QAr[lo:hi], QA[z0:z1]), (r.rank, "QA")
+        assert np.array_equal(QBr[lo:hi], QB[z0:z1]), (r.rank, "QB")
+    tab, H = G.glasma_tmunu(whole)
+    rows = T.gather_rows()
+    assert np.array_equal(rows, tab)
+    assert SL.total_energy(cfg, rows) == H
+    gw = G.glasma_gauss_residual(whole)
+    gs = [G.glasma_gauss_residual(r.h) for r in ranks]
+    assert max(g[0] for g in gs) == gw[0]
+    assert max(g[2] for g in gs) == gw[2]
+    # rms from the partial mean squares (summation order differs)
+    nz = cfg["nz"]
+    ms = sum(g[1] ** 2 * (r.z1 - r.z0) for g, r in zip(gs, ranks)) / nz
+    assert abs(np.sqrt(ms) - gw[1]) <= 1e-12 * gw[1]
+    # both nuclei crossed a slab boundary
+    assert any(np.any(G.glasma_get_fields(r.h)[3] != 0) for r in ranks[1:])
+
+
+@pytest.mark.parametrize("nc,precision,kernel", [
+    (2, "fp64", "auto"), (3, "fp64", "auto"), (3, "fp64", "staple"),
+    (2, "fp32", "staple"), (3, "fp32", "auto"), (3, "fp32", "plaquette")])
+@pytest.mark.parametrize("nranks", [2, 3])
+def test_slabs_match_the_whole_lattice(G, nc, precision, kernel, nranks):
+    """The ragged 47 x 10 x 12 collision (odd nz, uneven slabs) for 44 steps:
+    the nuclei meet at step 20 and the Glasma between them crosses the slab
+    boundaries."""
+    cfg = dict(gi.small_config(nc, nz=47, sigma_l=2.0), precision=precision)
+    whole, ranks, T = _run(G, cfg, nranks, 44, kernel)
+    _compare(G, cfg, whole, ranks, T)
+
+
+def test_slabs_with_the_64x64_plane(G):
+    """SU(3) FP64 with the 64 x 64 transverse plane (the plaquette kernel's
+    blocks of rows with a -y halo) on 3 slabs through the collision."""
+    cfg = dict(gi.small_config(3, nz=30, nx=64, ny=64, sigma_l=1.0), precision="fp64")
+    whole, ranks, T = _run(G, cfg, 3, 24, "auto")
+    _compare(G, cfg, whole, ranks, T)
+
+
+def test_slab_calls_reject_bad_use(G):
+    from paper_2009_02044_gb300 import slab as SL
+    cfg = gi.small_config(2, nz=47)
+    r = SL.SlabRank(cfg, 0, 2)
+    with pytest.raises(G.GlasmaError):          # windows not set yet
+        G.glasma_step(r.h, 1)
+    with pytest.raises(G.GlasmaError):          # no rank below rank 0
+        G.glasma_slab_pack(r.h, -1, r.buf[("send", +1)].data_ptr())
+    with pytest.raises(G.GlasmaError):
+        G.glasma_slab_init(dict(cfg, scheme="implicit"), 0, 20)
+    with pytest.raises(G.GlasmaError):
+        G.glasma_slab_init(cfg, 20, 60)
+    with pytest.raises(G.GlasmaError):          # checkpoints are whole lattices
+        G.glasma_get_state(r.h)
+    G.glasma_slab_set_windows(r.h, *SL.merge_windows([r.windows()]))
+    with pytest.raises(G.GlasmaError):          # one step per exchange
+        G.glasma_step(r.h, 2)

@@ -90,6 +90,23 @@ def test_kernel_matches_oracle_on_random_state(G, nc, shape, kernel):
         G.glasma_free(h)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_plaquette_result_does_not_depend_on_the_chunks(G, precision):
+    """Every chunk of z slices starts with a warm-up iteration of the same
+    code, so the state is bitwise the same for any chunk length (and for any
+    split of the lattice into slabs)."""
+    st = _random_state(3, 14, 40, 17, seed=5)
+    out = []
+    for zlen in (1, 3, 4, 14):
+        h = _ctx(G, st, precision)
+        G.glasma_set_step_kernel(h, "plaquette", zlen)
+        G.glasma_step(h, 3)
+        out.append(G.glasma_get_fields(h)[:4])
+    for other in out[1:]:
+        for x, y in zip(out[0], other):
+            assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("nc", [2, 3])
 @pytest.mark.parametrize("shape", [(8, 64, 64), (9, 37, 17), (13, 5, 9)])
 @pytest.mark.parametrize("kernel", KERNELS + ["staple_pairs"])
