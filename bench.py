@@ -35,7 +35,8 @@ Fields of the JSON line beyond the metric:
   extras        (unless --no-extras) the FP64 path and the FP32 energy-
                 density error against it, one T^{mu nu} sample, the improved
                 scheme on its 2048 x 128^2 workload, the batched ensemble,
-                the rest-frame analysis and the adjoint gradient
+                the rest-frame analysis, the adjoint gradient, and the
+                event split into z slabs with their halo exchange on one GPU
 """
 from __future__ import annotations
 
@@ -510,6 +511,7 @@ def run_extras(G, torch, cfg, args, stream, value):
     out["improved"] = run_improved(G, torch, stream)
     out["improved"]["fp32_error"] = run_improved_error(G, torch)
     out["ensemble"] = run_ensemble(G, torch, stream)
+    out["slab"] = run_slab(G, torch, stream, cfg)
     out["observables"] = run_observables(G, torch, stream)
     out["adjoint"] = run_adjoint(G, torch)
     return out
@@ -746,6 +748,72 @@ def run_ensemble(G, torch, stream, steps=40, warm=3):
             "batched_equals_sequential": bool(same),
             "eps_mean_peak": {"z": zpk, "value": float(mean[zpk]),
                               "event_std": float(eps[:, zpk].std(ddof=1))}}
+
+
+def run_slab(G, torch, stream, cfg, nranks=(2, 4), steps=100, warm=5):
+    """The z-slab decomposition (glasma_slab_*) of the benchmark event on
+    one GPU: P slab contexts (paper_2009_02044_gb300.slab) exchange their
+    halo slices by device copies before every step (LocalTransport: pack,
+    copy into the neighbour's buffer, unpack), the data path a multi-GPU run
+    sends over NCCL.  Reported per P: ms per step of all slabs with their
+    exchange against the whole lattice, the exchange alone, the halo bytes
+    per step, and whether the owned slices' T^{mu nu} rows and H equal the
+    whole lattice's bit for bit after the run."""
+    from paper_2009_02044_gb300 import slab as SL
+    V = cfg["nz"] * cfg["nx"] * cfg["ny"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    with torch.cuda.stream(stream):
+        whole = G.glasma_init_mv(cfg, None, stream=stream)
+    G.glasma_step(whole, warm)
+    ms_whole = timed(lambda: G.glasma_step(whole, steps))
+    tab_w, H_w = G.glasma_tmunu(whole)
+    G.glasma_free(whole)
+    out = {"workload": "%s (%d slices)" % ("su3_512x64x64", cfg["nz"]),
+           "steps_timed": steps, "whole_ms_per_step": ms_whole / steps,
+           "by_ranks": {},
+           "note": "one GPU; the exchange is device copies between slab "
+                   "contexts, not NCCL; multi-GPU unmeasured on hardware"}
+    for P in nranks:
+        with torch.cuda.stream(stream):
+            ranks = [SL.SlabRank(cfg, r, P, stream=stream) for r in range(P)]
+            T = SL.LocalTransport(ranks)
+            T.setup()
+
+            def run_steps(n):
+                for _ in range(n):
+                    T.step()
+
+            def run_exchanges(n):
+                for _ in range(n):
+                    T.exchange()
+
+            run_steps(warm)
+            ms = timed(lambda: run_steps(steps))
+            ms_x = timed(lambda: run_exchanges(steps))
+            T.exchange()
+            rows = T.gather_rows()
+        halo = sum(r.buf[("send", d)].numel() for r in ranks for d in (+1, -1)
+                   if r.has(d))
+        out["by_ranks"][str(P)] = {
+            "ms_per_step": ms / steps, "exchange_ms_per_step": ms_x / steps,
+            "over_whole": (ms / steps) / (ms_whole / steps),
+            "value": V * steps / (ms * 1e-3), "unit": METRIC,
+            "halo_bytes_per_step": halo,
+            "equals_whole_lattice": bool(np.array_equal(rows, tab_w)
+                                         and SL.total_energy(cfg, rows) == H_w)}
+        for r in ranks:
+            G.glasma_free(r.h)
+    return out
 
 
 def run_improved_error(G, torch, nt=16, steps=1000, every=50):

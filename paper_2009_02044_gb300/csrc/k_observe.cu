@@ -353,12 +353,12 @@ static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
-  // about 8 blocks per SM in all, at most kTmunuSplit per slice
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  // kTmunuSplit blocks per slice (fewer if the plane has fewer sites than
+  // threads): the split, and with it the order of each slice's sums, depends
+  // on the transverse plane alone, not on the number of slices or the device,
+  // so a z slab's rows equal the whole lattice's bit for bit
   const int64_t per_slice = (c->g.nxy + kRedThreads - 1) / kRedThreads;
-  int64_t split = (8 * (int64_t)sms + c->g.nz - 1) / c->g.nz;
-  if (split > kTmunuSplit) split = kTmunuSplit;
+  int64_t split = kTmunuSplit;
   if (split > per_slice) split = per_slice;
   if (split < 1) split = 1;
   a.split = (int)split;

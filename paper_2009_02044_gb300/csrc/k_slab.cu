@@ -28,33 +28,57 @@ size_t slab_msg_elems(const glasma_ctx* c, int dir) {
   return dir > 0 ? (size_t)(3 * 2 * nv + 2 * na) * nxy : (size_t)(2 * 2 * nv + na) * nxy;
 }
 
-// links of directions [0, ndir) on slice iz <-> buf[(d*nv + k)*nxy + t]
-template <typename V2, bool PACK>
-__global__ void k_slab_links(V2* U, int nc, int nv, int64_t V, int64_t nxy, int iz, int ndir, V2* buf) {
-  const int64_t n = (int64_t)ndir * nv * nxy;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = i % nxy, dk = i / nxy;
-    const int k = (int)(dk % nv), d = (int)(dk / nv);
-    const int64_t e = link_index(nc, d, k, V, (int64_t)iz * nxy + t);
-    if (PACK)
-      buf[i] = U[e];
-    else
-      U[e] = buf[i];
-  }
-}
+// One message <-> its slice, in one launch: work item i < nl is a link
+// component (V2 units), buf[i] <-> U at link (d, k) of site iz*nxy + t with
+// i = (d*nv + k)*nxy + t; the items after it are reals, first the E_z rows
+// (up messages), E[c*V + e_off + t], then the charge rows Q[c*q_stride +
+// q_off + t].  A charge slice outside the nucleus' window is not present:
+// pack writes zeros, unpack skips it.
+template <typename R>
+struct SlabIOArgs {
+  typename V2T<R>::T* U;
+  R* E;
+  R* Q;
+  R* buf;
+  int64_t V, nxy, nl, e_off, q_stride, q_off;
+  int nc, nv, na, iz;
+  int has_e, q_present;
+};
 
-// comps rows of nxy reals at field[c*stride + off + t] <-> buf[c*nxy + t];
-// present = false: the rows do not exist here (pack writes zeros, unpack
-// skips)
 template <typename R, bool PACK>
-__global__ void k_slab_rows(R* field, int comps, int64_t stride, int64_t off, int64_t nxy, bool present, R* buf) {
-  const int64_t n = (int64_t)comps * nxy;
+__global__ void k_slab_io(SlabIOArgs<R> a) {
+  typedef typename V2T<R>::T V2;
+  const int64_t nrows = (int64_t)(a.has_e ? 2 : 1) * a.na * a.nxy;
+  const int64_t n = a.nl + nrows;
+  V2* lb = (V2*)a.buf;
+  R* rb = a.buf + 2 * a.nl;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = i % nxy, c = i / nxy;
-    if (PACK)
-      buf[i] = present ? field[c * stride + off + t] : R(0);
-    else if (present)
-      field[c * stride + off + t] = buf[i];
+    if (i < a.nl) {
+      const int64_t t = i % a.nxy, dk = i / a.nxy;
+      const int k = (int)(dk % a.nv), d = (int)(dk / a.nv);
+      const int64_t e = link_index(a.nc, d, k, a.V, (int64_t)a.iz * a.nxy + t);
+      if (PACK)
+        lb[i] = a.U[e];
+      else
+        a.U[e] = lb[i];
+    } else {
+      const int64_t j = i - a.nl;
+      const int64_t t = j % a.nxy;
+      const int64_t c = j / a.nxy;
+      if (a.has_e && c < a.na) {
+        R* f = a.E + c * a.V + a.e_off + t;
+        if (PACK)
+          rb[j] = *f;
+        else
+          *f = rb[j];
+      } else {
+        const int64_t cq = a.has_e ? c - a.na : c;
+        if (PACK)
+          rb[j] = a.q_present ? a.Q[cq * a.q_stride + a.q_off + t] : R(0);
+        else if (a.q_present)
+          a.Q[cq * a.q_stride + a.q_off + t] = rb[j];
+      }
+    }
   }
 }
 
@@ -65,40 +89,35 @@ static unsigned grid_of(int64_t n) {
 
 template <typename R>
 static int slab_io(glasma_ctx* c, int dir, void* buf, bool pack) {
-  typedef typename V2T<R>::T V2;
-  const int64_t nxy = c->g.nxy, V = c->g.V;
-  const int na = c->na, nv = c->nv;
-  V2* U = (V2*)c->U[c->cur];
-  R* b = (R*)buf;
+  SlabIOArgs<R> a;
+  a.nxy = c->g.nxy;
+  a.V = c->g.V;
+  a.na = c->na;
+  a.nv = c->nv;
+  a.nc = c->p.nc;
+  a.U = (typename V2T<R>::T*)c->U[c->cur];
+  a.E = (R*)c->E;
+  a.buf = (R*)buf;
   // dir +1: my top owned slice (pack) or, unpacking a message from below,
   // my lower halo slice; dir -1 likewise the other side
   const bool up_msg = pack ? dir > 0 : dir < 0;
-  const int iz = pack ? (dir > 0 ? c->hi - 1 : c->lo) : (dir < 0 ? 0 : c->hi);
+  a.iz = pack ? (dir > 0 ? c->hi - 1 : c->lo) : (dir < 0 ? 0 : c->hi);
   const int ndir = up_msg ? 3 : 2;
-  const int64_t nl = (int64_t)ndir * nv * nxy;
-  if (pack)
-    k_slab_links<V2, true><<<grid_of(nl), 256, 0, c->stream>>>(U, c->p.nc, nv, V, nxy, iz, ndir, (V2*)b);
-  else
-    k_slab_links<V2, false><<<grid_of(nl), 256, 0, c->stream>>>(U, c->p.nc, nv, V, nxy, iz, ndir, (V2*)b);
-  R* rest = b + 2 * nl;
-  if (up_msg) {  // E_z of the slice
-    const int64_t off = (int64_t)2 * na * V + (int64_t)iz * nxy;
-    if (pack)
-      k_slab_rows<R, true><<<grid_of(na * nxy), 256, 0, c->stream>>>((R*)c->E, na, V, off, nxy, true, rest);
-    else
-      k_slab_rows<R, false><<<grid_of(na * nxy), 256, 0, c->stream>>>((R*)c->E, na, V, off, nxy, true, rest);
-    rest += (int64_t)na * nxy;
-  }
+  a.nl = (int64_t)ndir * a.nv * a.nxy;
+  a.has_e = up_msg ? 1 : 0;  // E_z of the slice
+  a.e_off = (int64_t)2 * a.na * a.V + (int64_t)a.iz * a.nxy;
   // the charge of B (up) or A (down) on the slice, if in the window
-  R* Q = (R*)(up_msg ? c->QB : c->QA);
+  a.Q = (R*)(up_msg ? c->QB : c->QA);
   const int z0 = up_msg ? c->zB0 : c->zA0, W = up_msg ? c->WB : c->WA;
-  const int k = iz - z0;
-  const bool present = k >= 0 && k < W;
-  const int64_t stride = (int64_t)W * nxy, off = present ? (int64_t)k * nxy : 0;
+  const int k = a.iz - z0;
+  a.q_present = (k >= 0 && k < W) ? 1 : 0;
+  a.q_stride = (int64_t)W * a.nxy;
+  a.q_off = a.q_present ? (int64_t)k * a.nxy : 0;
+  const int64_t n = a.nl + (int64_t)(a.has_e ? 2 : 1) * a.na * a.nxy;
   if (pack)
-    k_slab_rows<R, true><<<grid_of(na * nxy), 256, 0, c->stream>>>(Q, na, stride, off, nxy, present, rest);
+    k_slab_io<R, true><<<grid_of(n), 256, 0, c->stream>>>(a);
   else
-    k_slab_rows<R, false><<<grid_of(na * nxy), 256, 0, c->stream>>>(Q, na, stride, off, nxy, present, rest);
+    k_slab_io<R, false><<<grid_of(n), 256, 0, c->stream>>>(a);
   return cuda_check(cudaGetLastError(), pack ? "slab pack" : "slab unpack");
 }
 

@@ -88,6 +88,23 @@ def test_slabs_with_the_64x64_plane(G):
     _compare(G, cfg, whole, ranks, T)
 
 
+def test_slab_rows_on_a_long_lattice(G):
+    """SU(3) FP32 with 256 slices of 64 x 64 on 2 slabs: each slice's
+    T^{mu nu} sums take the same order whatever the number of slices a
+    context holds (the whole lattice's 256 against a slab's 129), so the
+    gathered rows and H equal the whole lattice's bit for bit."""
+    from paper_2009_02044_gb300 import slab as SL
+    cfg = dict(gi.CONFIGS["su3_512x64x64"], nz=256, precision="fp32")
+    whole, ranks, T = _run(G, cfg, 2, 4, "auto")
+    tab, H = G.glasma_tmunu(whole)
+    rows = T.gather_rows()
+    assert np.array_equal(rows, tab)
+    assert SL.total_energy(cfg, rows) == H
+    for r in ranks:
+        G.glasma_free(r.h)
+    G.glasma_free(whole)
+
+
 def test_slab_calls_reject_bad_use(G):
     from paper_2009_02044_gb300 import slab as SL
     cfg = gi.small_config(2, nz=47)
