@@ -86,9 +86,14 @@ def make_slab(st: O.State, z0, z1):
     for k in list(range(lo)) + list(range(hi, g1 - g0)):
         U[:, k] = np.eye(p.nc)
         E[:, k] = 0.0
+    Up = None
+    if st.U_prev is not None:
+        Up = st.U_prev[:, g0:g1].copy()
+        for k in list(range(lo)) + list(range(hi, g1 - g0)):
+            Up[:, k] = np.eye(p.nc)
     # charges live only on owned slices; halo charges arrive by exchange
     _clear_halo_charges(QA, QB, lo, hi)
-    return Slab(O.State(pl, U, E, QA, QB, st.n), z0, z1, lo, hi, p.nz)
+    return Slab(O.State(pl, U, E, QA, QB, st.n, Up), z0, z1, lo, hi, p.nz)
 
 
 def _clear_halo_charges(QA, QB, lo, hi):
@@ -100,9 +105,13 @@ def _clear_halo_charges(QA, QB, lo, hi):
 
 def message_up(s: Slab):
     """To the rank above: links (3 directions), E_z and nucleus B's charge of
-    the top owned slice."""
+    the top owned slice; under the improved scheme also its z links at
+    t_{n-1} (the t_{n-1} slot's z staples of the slice above)."""
     k = s.hi - 1
-    return dict(U=s.st.U[:, k].copy(), Ez=s.st.E[2][k].copy(), QB=s.st.QB[k].copy())
+    m = dict(U=s.st.U[:, k].copy(), Ez=s.st.E[2][k].copy(), QB=s.st.QB[k].copy())
+    if s.st.U_prev is not None:
+        m["Uprev_z"] = s.st.U_prev[2][k].copy()
+    return m
 
 
 def message_down(s: Slab):
@@ -116,6 +125,8 @@ def receive_from_below(s: Slab, m):
     s.st.U[:, 0] = m["U"]
     s.st.E[2][0] = m["Ez"]
     s.st.QB[0] = m["QB"]
+    if "Uprev_z" in m:
+        s.st.U_prev[2][0] = m["Uprev_z"]
 
 
 def receive_from_above(s: Slab, m):
@@ -178,3 +189,79 @@ def exchange_in_process(slabs):
             receive_from_below(s, ups[r - 1])
         if s.has_above:
             receive_from_above(s, downs[r + 1])
+
+
+# ---------------------------------------------------------------------------
+# The improved scheme (oracle.glasma_oracle.step_implicit) on slabs.
+#
+# Its fixed-point sweeps couple the slices through the iterate U(t_{n+1}),
+# but only through z links: in a plane containing z only the z links take
+# the time slot, the transverse links stay at t_n.  The force on the z link
+# of slice z then reads the z links of slice z at every slot and the
+# transverse links of slices z and z + 1 at t_n; so each rank evaluates the
+# z link of its lower halo slice itself, every sweep, from what the step's
+# halo brings (the links at t_n of both halo slices, E_z and U(t_{n-1})'s z
+# link of the lower one, the charges whose hop crosses it), with the same
+# arithmetic as its owner, and no sweep needs a message.  What couples the
+# ranks is the stopping test: it takes the largest change of E over the
+# whole lattice, i.e. each rank's maximum over its owned slices folded with
+# max across ranks, so every rank stops after the same sweep as the
+# monolithic step.
+# ---------------------------------------------------------------------------
+
+def implicit_begin(s: Slab):
+    """Hop (the leapfrog's, from U(t_n)) and the first iterate
+    U(t_{n+1}) = exp(i dt E(t_{n-1/2})) U(t_n) of the local lattice."""
+    st = s.st
+    QA, QB, djz = O.hop(st)
+    s.work = dict(QA=QA, QB=QB, djz=djz, Ek=st.E, X=O.u_update(st.U, st.E, st.p))
+
+
+def implicit_sweep(s: Slab, w=O.IMPLICIT_WEIGHTS):
+    """One sweep: E^(k+1) = E(t_{n-1/2}) + dt F(X^(k), U(t_n), U(t_{n-1}))
+    + dt J, X^(k+1) = exp(i dt E^(k+1)) U(t_n).  Returns the largest change
+    of E over the owned slices."""
+    st, W = s.st, s.work
+    p = st.p
+    F = O.force_implicit((W["X"], st.U, st.U_prev), p, w)
+    En = st.E + p.dt * F
+    En[2] = En[2] + W["djz"]
+    En[2] = np.where(O.link_mask(2, p.nz, p.ny, p.nx)[..., None], En[2], 0.0)
+    delta = float(np.max(np.abs(En - W["Ek"])[:, s.lo:s.hi]))
+    W["Ek"] = En
+    W["X"] = O.u_update(st.U, En, p)
+    return delta
+
+
+def implicit_end(s: Slab, iters):
+    """Commit the step: the last iterate and its E; U(t_n) becomes U_prev."""
+    W = s.work
+    s.st = O.State(s.st.p, W["X"], W["Ek"], W["QA"], W["QB"], s.st.n + 1, s.st.U,
+                   dict(s.st.extra, iters=iters))
+    _clear_halo_charges(s.st.QA, s.st.QB, s.lo, s.hi)
+    s.work = None
+
+
+def run_implicit_in_process(st: O.State, nranks, steps, w=O.IMPLICIT_WEIGHTS,
+                            tol=1e-14, max_iter=100, on_sweep=None):
+    """The improved scheme on nranks slabs of one process; every sweep's
+    largest change is the max over the ranks' owned slices.  on_sweep(slabs)
+    is called after every sweep (for checks).  Returns the slabs after
+    `steps`, each with its sweep count in st.extra["iters"]."""
+    slabs = [make_slab(st, z0, z1) for z0, z1 in slab_bounds(st.p.nz, nranks)]
+    for _ in range(steps):
+        exchange_in_process(slabs)
+        for s in slabs:
+            implicit_begin(s)
+        for it in range(max_iter):
+            delta = max(implicit_sweep(s, w) for s in slabs)
+            if on_sweep:
+                on_sweep(slabs)
+            if delta < tol:
+                break
+        else:
+            raise O.NotConverged("implicit step did not converge")
+        for s in slabs:
+            implicit_end(s, it + 1)
+    exchange_in_process(slabs)
+    return slabs
