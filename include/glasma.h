@@ -302,10 +302,10 @@ GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
  *   glasma_init_mv, every rank passing the same p and charges).  Its local
  *   lattice is the slab plus a halo slice below (if z0 > 0) and above (if
  *   z1 < nz); the initial state of every owned and halo slice equals the
- *   whole lattice's bit for bit.  Leapfrog scheme only.  The step kernel is
- *   the staple or plaquette kernel (never the site-paired one).  Errors:
- *   INVALID_ARG (as glasma_init_mv; z0 < 0, z1 > nz, z1 <= z0; implicit
- *   scheme), OOM, CUDA.
+ *   whole lattice's bit for bit.  The leapfrog step kernel is the staple or
+ *   plaquette kernel (never the site-paired one); the improved scheme runs
+ *   sweep by sweep (glasma_implicit_begin below).  Errors: INVALID_ARG (as
+ *   glasma_init_mv; z0 < 0, z1 > nz, z1 <= z0), OOM, CUDA.
  * glasma_slab_info: owned global slices [*z0, *z1), local slices, and the
  *   local indices [*lo, *hi) of the owned slices (any pointer may be NULL).
  * glasma_slab_set_windows: the charge windows of the whole lattice (first
@@ -330,7 +330,9 @@ GLASMA_API int glasma_get_info(const glasma_ctx* c, glasma_info* info);
  *   rank above; asynchronous on the context's stream.
  * Protocol per step: every rank packs its messages, sends them, receives
  *   its neighbours' and unpacks them, then calls glasma_step(c, 1) (a slab
- *   context takes one step per exchange).  glasma_tmunu then returns the
+ *   context takes one step per exchange), or under the improved scheme
+ *   glasma_implicit_begin, sweeps with the maxima folded across the ranks,
+ *   and glasma_implicit_end (below).  glasma_tmunu then returns the
  *   z1 - z0 rows of the owned slices and their partial energy (the whole
  *   lattice's H is the sum of the gathered rows in z order),
  *   glasma_gauss_residual the residual over the owned slices, and
@@ -436,6 +438,38 @@ GLASMA_API int glasma_fit_gaussian(const double* x, const double* f, int n, doub
  */
 GLASMA_API int glasma_implicit_converged(const double* dmax, const double* emax, int k, double tol, int precision,
                                          int* converged);
+
+/*
+ * The improved step (Sec. 3, the paragraph after Eq. gauss; Fig. wilson (b))
+ * driven sweep by sweep from the host, the form a lattice split into z
+ * slabs needs: the stopping rule takes the largest change of E over the
+ * whole lattice, so each rank's sweep maxima are folded (max) across the
+ * ranks before the test.  The sweeps need no halo messages (in a plane
+ * containing z only the z links take the time slot of the iterate, and the
+ * z link of the lower halo slice is evaluated on the slab from the step's
+ * halo, with its owner's arithmetic); the step's halo exchange comes before
+ * glasma_implicit_begin.  Any context of the improved scheme may use these
+ * calls; glasma_step does the same for a whole lattice with every sweep
+ * queued at once.
+ * glasma_implicit_begin: the CPIC hop, U(t_{n-1}) on the first step, the
+ *   first iterate U(t_{n+1}) = exp(i dt E(t_{n-1/2})) U(t_n) and the force
+ *   of the time slots t_n and t_{n-1}.  Errors: INVALID_ARG (leapfrog
+ *   context, a step already begun, slab windows not set), PARTICLE_EXIT,
+ *   CUDA.
+ * glasma_implicit_sweep: one sweep (E = E(t_{n-1/2}) + dt J + dt F, the
+ *   next iterate), synchronising the stream; *dmax = max |E^(k+1) - E^(k)|
+ *   and *emax = max |E^(k+1)| over the owned slices.  The caller folds them
+ *   across ranks and applies glasma_implicit_converged to the folded
+ *   sequence.  Errors: INVALID_ARG (no step begun, NULL pointers),
+ *   NOT_CONVERGED (implicit_max_iter sweeps already done), CUDA.
+ * glasma_implicit_end: commit the last sweep's iterate as U(t_{n+1}) and
+ *   its E as E(t_{n+1/2}), move the charge windows of a hop step, advance
+ *   the step counter (glasma_get_info reports the sweeps).  Errors:
+ *   INVALID_ARG (no step begun, no sweep done).
+ */
+GLASMA_API int glasma_implicit_begin(glasma_ctx* c);
+GLASMA_API int glasma_implicit_sweep(glasma_ctx* c, double* dmax, double* emax);
+GLASMA_API int glasma_implicit_end(glasma_ctx* c);
 
 /*
  * Gradient of the mid-rapidity energy with respect to the initial MV colour

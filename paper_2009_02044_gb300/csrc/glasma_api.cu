@@ -279,8 +279,6 @@ int glasma_init_mv(const glasma_params* p, const double* rho_host, void* stream,
 int glasma_slab_init(const glasma_params* p, const double* rho_host, int z0, int z1, void* stream,
                      const glasma_allocator* alloc, glasma_ctx** out) {
   if (!p) return set_error(GLASMA_ERR_INVALID_ARG, "params is NULL");
-  if (p->scheme != GLASMA_LEAPFROG)
-    return set_error(GLASMA_ERR_INVALID_ARG, "slab contexts run the leapfrog scheme");
   return create_ctx(p, rho_host, stream, alloc, z0, z1, out);
 }
 
@@ -290,6 +288,10 @@ int glasma_step(glasma_ctx* c, int n_steps) {
     return set_error(GLASMA_ERR_INVALID_ARG, "a slab context needs glasma_slab_set_windows before stepping");
   if (c->slab && n_steps > 1)
     return set_error(GLASMA_ERR_INVALID_ARG, "a slab context takes one step per halo exchange");
+  if (c->slab && c->p.scheme == GLASMA_IMPLICIT)
+    return set_error(GLASMA_ERR_INVALID_ARG,
+                     "a slab context takes the improved step sweep by sweep (glasma_implicit_begin/_sweep/_end)");
+  if (c->impl_active) return set_error(GLASMA_ERR_INVALID_ARG, "an improved step is in progress (glasma_implicit_end)");
   cudaSetDevice(c->device);
   int launches = 0;
   for (int k = 0; k < n_steps; ++k) {
@@ -331,6 +333,58 @@ int glasma_step(glasma_ctx* c, int n_steps) {
     }
   }
   c->last_launches = launches;
+  return GLASMA_OK;
+}
+
+// exit checks of a hop step, in global slices (a slab's windows are the
+// whole lattice's)
+static int hop_exit_check(const glasma_ctx* c) {
+  if (c->WB > 0 && c->zB0 + c->zoff + c->WB - 1 >= c->nz_glob - 1)
+    return set_error(GLASMA_ERR_PARTICLE_EXIT, "nucleus B reached the upper z boundary");
+  if (c->WA > 0 && c->zA0 + c->zoff <= 0)
+    return set_error(GLASMA_ERR_PARTICLE_EXIT, "nucleus A reached the lower z boundary");
+  return GLASMA_OK;
+}
+
+int glasma_implicit_begin(glasma_ctx* c) {
+  if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
+  if (c->p.scheme != GLASMA_IMPLICIT) return set_error(GLASMA_ERR_INVALID_ARG, "the context runs the leapfrog scheme");
+  if (c->impl_active) return set_error(GLASMA_ERR_INVALID_ARG, "an improved step is already in progress");
+  if (c->slab && !c->slab_windows)
+    return set_error(GLASMA_ERR_INVALID_ARG, "a slab context needs glasma_slab_set_windows before stepping");
+  cudaSetDevice(c->device);
+  const bool hop = hop_at(c->n, c->hop_p, c->hop_q);
+  int st = hop ? hop_exit_check(c) : GLASMA_OK;
+  if (!st) st = implicit_begin(c, hop);
+  if (st) return st;
+  c->impl_active = true;
+  c->impl_hop = hop;
+  c->impl_k = 0;
+  return GLASMA_OK;
+}
+
+int glasma_implicit_sweep(glasma_ctx* c, double* dmax, double* emax) {
+  if (!c || !dmax || !emax) return set_error(GLASMA_ERR_INVALID_ARG, "bad arguments");
+  if (!c->impl_active) return set_error(GLASMA_ERR_INVALID_ARG, "no improved step in progress (glasma_implicit_begin)");
+  if (c->impl_k >= c->p.implicit_max_iter)
+    return set_error(GLASMA_ERR_NOT_CONVERGED, "implicit_max_iter sweeps already done in this step");
+  cudaSetDevice(c->device);
+  return implicit_sweep(c, dmax, emax);
+}
+
+int glasma_implicit_end(glasma_ctx* c) {
+  if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
+  if (!c->impl_active || c->impl_k < 1)
+    return set_error(GLASMA_ERR_INVALID_ARG, "no improved step with at least one sweep in progress");
+  implicit_commit(c, c->impl_k);
+  if (c->impl_hop) {
+    c->zB0 += 1;
+    c->zA0 -= 1;
+  }
+  c->n += 1;
+  c->last_iters = c->impl_k;
+  c->last_launches = c->impl_k + 1;
+  c->impl_active = false;
   return GLASMA_OK;
 }
 

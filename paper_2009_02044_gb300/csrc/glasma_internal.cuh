@@ -50,6 +50,10 @@ struct glasma_ctx {
   bool slab = false;
   bool slab_windows = false;  // the windows hold the whole lattice's extent
   int zoff = 0, lo = 0, hi = 0, nz_glob = 0;
+  // improved step driven sweep by sweep from the host (glasma_implicit_*)
+  bool impl_active = false;   // between glasma_implicit_begin and _end
+  bool impl_hop = false;      // that step is a hop step
+  int impl_k = 0;             // sweeps done in it
   struct Alloc {
     void* ptr;
     size_t bytes;
@@ -96,6 +100,12 @@ int plaq_default_zlen(const glasma_ctx* c);
 // any capture of its launches)
 int plaq_prepare(glasma_ctx* c);
 int launch_step_implicit(glasma_ctx* c, bool hop, int* iters);
+// the same step in host-driven parts (k_implicit.cu): the hop, U(t_{n-1}) if
+// needed and the first iterate; one sweep (index c->impl_k) with its
+// maxima read back; the commit of the last iterate after `done` sweeps
+int implicit_begin(glasma_ctx* c, bool hop);
+int implicit_sweep(glasma_ctx* c, double* dmax, double* emax);
+void implicit_commit(glasma_ctx* c, int done);
 int launch_gauss(glasma_ctx* c, double* out3);  // over the owned slices [lo, hi)
 // slab halo messages (k_slab.cu)
 size_t slab_msg_elems(const glasma_ctx* c, int dir);

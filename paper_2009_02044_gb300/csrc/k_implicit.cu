@@ -21,6 +21,17 @@
 // precision (always first in FP32).  Every launch after that returns at
 // once; if it never holds within implicit_max_iter the step reports
 // NOT_CONVERGED.
+//
+// On a z slab (glasma_slab_init) the step runs in host-driven parts
+// (glasma_implicit_begin / _sweep / _end): every sweep's maxima are read
+// back, folded across the ranks, and the host applies the stopping test.
+// The sweeps need no halo messages: in a plane containing z only the z
+// links take the time slot, so the force on a z link reads z links of its
+// own slice and transverse links at t_n of its slice and the one above.
+// So each part also evaluates the z link of the lower halo slice (one more
+// launch over that slice: k_implicit_prep_halo, k_implicit_iter_halo), from
+// the step's halo and with its owner's arithmetic, including the hop of the
+// charges that cross it; the maxima stay those of the owned slices.
 #include <vector>
 
 #include "glasma_internal.cuh"
@@ -77,6 +88,8 @@ struct ImplArgs {
   R az2;
   int hop;
   int zA0, WA, zB0, WB;
+  int zlo, zhi;   // slices of the prepare and sweep kernels: the owned ones
+  int check;      // sweeps return at once after convergence (device test)
 };
 
 // Link buffer of slot m for a link of direction d in plane (i, j).
@@ -224,22 +237,57 @@ __device__ __forceinline__ void prep_link(const ImplArgs<R>& a, int i, uint32_t 
 // 87 -> 70 ms per step of the SU(3) 2048 x 128^2 workload.
 constexpr int kImplZ = 16;
 
-template <int NC, typename R>
+// SLAB: the owned slices start at zlo (a whole lattice's at 0, fixed at
+// compile time: the offset costs the 80-register sweep 12 B of spills).
+template <int NC, typename R, bool SLAB>
 __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_prep(ImplArgs<R> a) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int z0 = (int)blockIdx.y * kImplZ;
+  const int z0 = (SLAB ? a.zlo : 0) + (int)blockIdx.y * kImplZ;
 #pragma unroll 1
-  for (int k = 0; k < kImplZ && z0 + k < a.g.nz; ++k) prep_link<NC, R>(a, (int)threadIdx.y, t, z0 + k);
+  for (int k = 0; k < kImplZ && z0 + k < a.zhi; ++k) prep_link<NC, R>(a, (int)threadIdx.y, t, z0 + k);
+}
+
+// The z links of a slab's lower halo slice (zlo - 1), as its owner prepares
+// them.
+template <int NC, typename R>
+__global__ void __launch_bounds__(64) k_implicit_prep_halo(ImplArgs<R> a) {
+  prep_link<NC, R>(a, 2, blockIdx.x * blockDim.x + threadIdx.x, a.zlo - 1);
+}
+
+// Link i at (t, iz) in one sweep: E = Ework + dt F_0(X), Xn = exp(i dt E)
+// U_n; the largest change and the largest E component go to dmax, emax.
+template <int NC, typename R>
+__device__ __forceinline__ void sweep_link(const ImplArgs<R>& a, int i, uint32_t t, int iz, R& dmax, R& emax) {
+  typedef LinkAlg<NC, R> G;
+  typedef typename G::M M;
+  constexpr int NA = G::NA;
+  const SiteNbr n = site_nbr_tz(a.g, t, iz);
+  const int64_t s = n.s;
+  R F[NA];
+  force_implicit<NC, R>(a, n, i, F, 0, 1);
+  R e[NA];
+#pragma unroll
+  for (int c = 0; c < NA; ++c) {
+    const int64_t idx = (int64_t)(i * NA + c) * a.g.V + s;
+    e[c] = a.Ework[idx] + a.dt * F[c];
+    const R d = fabs(e[c] - a.E[idx]);
+    dmax = isfinite(d) ? fmax(dmax, d) : R(INFINITY);
+    emax = fmax(emax, fabs(e[c]));
+    a.E[idx] = e[c];
+  }
+  M u = G::mul(G::expi_series(e, a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
+  if (sizeof(R) == 4) u = G::reunit(u);
+  LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
 }
 
 // One fixed-point sweep: E = Ework + dt F_0(X), Xn = exp(i dt E) U_n, where
 // Ework already holds E(t_{n-1/2}) + dt J + dt (F_1(U_n) + F_2(U_{n-1})).
-template <int NC, typename R>
+template <int NC, typename R, bool SLAB>
 __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplArgs<R> a) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  if (a.k > 0 && implicit_converged(a.conv, a.maxit, a.k - 1, a.tol, sizeof(R) == 4)) return;
+  if (a.check && a.k > 0 && implicit_converged(a.conv, a.maxit, a.k - 1, a.tol, sizeof(R) == 4)) return;
   // The maxima are taken in the state's precision (the largest change of
   // an FP32 field, rounded once to FP32, is all the convergence test needs)
   // and converted to FP64 once per block: per-element FP64 arithmetic would
@@ -248,28 +296,12 @@ __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplA
   const int i = (int)threadIdx.y;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   R dmax = R(0), emax = R(0);
-  const int z0 = (int)blockIdx.y * kImplZ;
+  const int z0 = (SLAB ? a.zlo : 0) + (int)blockIdx.y * kImplZ;
 #pragma unroll 1
-  for (int kz = 0; kz < kImplZ && z0 + kz < a.g.nz; ++kz) {
+  for (int kz = 0; kz < kImplZ && z0 + kz < a.zhi; ++kz) {
     const int iz = z0 + kz;
     if (t >= (uint32_t)a.g.nxy || (i == 2 && iz == a.g.nz - 1)) continue;
-    const SiteNbr n = site_nbr_tz(a.g, t, iz);
-    const int64_t s = n.s;
-    R F[NA];
-    force_implicit<NC, R>(a, n, i, F, 0, 1);
-    R e[NA];
-#pragma unroll
-    for (int c = 0; c < NA; ++c) {
-      const int64_t idx = (int64_t)(i * NA + c) * a.g.V + s;
-      e[c] = a.Ework[idx] + a.dt * F[c];
-      const R d = fabs(e[c] - a.E[idx]);
-      dmax = isfinite(d) ? fmax(dmax, d) : R(INFINITY);
-      emax = fmax(emax, fabs(e[c]));
-      a.E[idx] = e[c];
-    }
-    M u = G::mul(G::expi_series(e, a.dt), LinkIO<NC, R>::template load<R>(a.Un, i, a.g.V, s));
-    if (sizeof(R) == 4) u = G::reunit(u);
-    LinkIO<NC, R>::template store<R>(a.Xn, i, a.g.V, s, u);
+    sweep_link<NC, R>(a, i, t, iz, dmax, emax);
   }
   // block max: warp shuffles, then one value per warp
 #pragma unroll
@@ -294,8 +326,20 @@ __global__ void __launch_bounds__(192, ImplOcc<R>::blocks) k_implicit_iter(ImplA
   }
 }
 
+// The z links of a slab's lower halo slice (zlo - 1) in one sweep, as their
+// owner evaluates them; their changes belong to the owner's maxima.
 template <int NC, typename R>
-static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
+__global__ void __launch_bounds__(64) k_implicit_iter_halo(ImplArgs<R> a) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (uint32_t)a.g.nxy) return;
+  R dmax = R(0), emax = R(0);
+  sweep_link<NC, R>(a, 2, t, a.zlo - 1, dmax, emax);
+}
+
+// Arguments of the prepare and sweep kernels (the iterate buffers and the
+// sweep index are set by the caller).
+template <typename R>
+static ImplArgs<R> impl_args(glasma_ctx* c, bool hop) {
   typedef typename V2T<R>::T V2;
   ImplArgs<R> a;
   a.E = (R*)c->E;
@@ -304,6 +348,8 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   a.QB = (R*)c->QB;
   a.conv = c->conv;
   a.tol = c->p.implicit_tol;
+  a.maxit = c->p.implicit_max_iter;
+  a.k = 0;
   a.g = c->g;
   a.dt = (R)c->p.dt;
   a.w[0] = (R)(2.0 / (c->p.a_t * c->p.a_t));
@@ -315,39 +361,99 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   a.WA = c->WA;
   a.zB0 = c->zB0;
   a.WB = c->WB;
-  void* prev = c->Uprev;
-  void* now = c->U[c->cur];
-  void* xa = c->U[1 - c->cur];
-  void* xb = c->Uit;
-  a.Up = (const V2*)prev;
-  a.Un = (const V2*)now;
-  // 64 transverse sites x the three directions per block, one row of
-  // blocks per z slice (the directions share neighbour links in L1)
+  a.Up = (const V2*)c->Uprev;
+  a.Un = (const V2*)c->U[c->cur];
+  a.X = nullptr;
+  a.Xn = nullptr;
+  a.Uout = nullptr;
+  a.zlo = c->lo;
+  a.zhi = c->hi;
+  a.check = 1;
+  return a;
+}
+
+// 64 transverse sites x the three directions per block; a row of blocks
+// per kImplZ owned slices
+static dim3 impl_grid(const glasma_ctx* c) {
+  return dim3((unsigned)((c->g.nxy + 63) / 64), (unsigned)((c->hi - c->lo + kImplZ - 1) / kImplZ));
+}
+
+// U(t_{n-1}) if unknown, the cleared maxima, and the prepare kernel (hop,
+// first iterate into U[1 - cur], work field).
+template <int NC, typename R>
+static int implicit_prepare(glasma_ctx* c, bool hop) {
+  typedef typename V2T<R>::T V2;
+  ImplArgs<R> a = impl_args<R>(c, hop);
   const dim3 bs(64, 3);
-  const dim3 grid((unsigned)((c->g.nxy + 63) / 64), (unsigned)c->g.nz);
-  const dim3 gridz(grid.x, (unsigned)((c->g.nz + kImplZ - 1) / kImplZ));
   int st;
   if (!c->uprev_valid) {
-    a.Uout = (V2*)prev;
+    // every local slice, halos included: a lower halo's z link at t_{n-1}
+    // follows from its E_z and U_z, which the step's halo brings
+    a.Uout = (V2*)c->Uprev;
+    const dim3 grid((unsigned)((c->g.nxy + 63) / 64), (unsigned)c->g.nz);
     k_implicit_prev<NC, R><<<grid, bs, 0, c->stream>>>(a);
     st = cuda_check(cudaGetLastError(), "k_implicit_prev launch");
     if (st) return st;
     c->uprev_valid = true;
   }
-  const int maxit = c->p.implicit_max_iter;
-  a.maxit = maxit;
-  st = cuda_check(cudaMemsetAsync(c->conv, 0, sizeof(double) * 2 * (maxit + 1), c->stream), "conv clear");
+  st = cuda_check(cudaMemsetAsync(c->conv, 0, sizeof(double) * 2 * (a.maxit + 1), c->stream), "conv clear");
   if (st) return st;
-  a.Xn = (V2*)xa;
-  k_implicit_prep<NC, R><<<gridz, bs, 0, c->stream>>>(a);
+  a.Xn = (V2*)c->U[1 - c->cur];
+  if (c->lo > 0)
+    k_implicit_prep<NC, R, true><<<impl_grid(c), bs, 0, c->stream>>>(a);
+  else
+    k_implicit_prep<NC, R, false><<<impl_grid(c), bs, 0, c->stream>>>(a);
   st = cuda_check(cudaGetLastError(), "k_implicit_prep launch");
+  if (st || c->lo == 0) return st;
+  k_implicit_prep_halo<NC, R><<<(unsigned)((c->g.nxy + 63) / 64), 64, 0, c->stream>>>(a);
+  return cuda_check(cudaGetLastError(), "k_implicit_prep_halo launch");
+}
+
+// Iterate buffers of sweep k: it reads xa for even k and xb for odd k
+// (xa = U[1 - cur] holds the first iterate, xb = Uit) and writes the other.
+template <int NC, typename R>
+static int implicit_launch_sweep(glasma_ctx* c, bool hop, int k, bool check) {
+  typedef typename V2T<R>::T V2;
+  ImplArgs<R> a = impl_args<R>(c, hop);
+  void* xa = c->U[1 - c->cur];
+  void* xb = c->Uit;
+  a.k = k;
+  a.check = check ? 1 : 0;
+  a.X = (const V2*)(k % 2 == 0 ? xa : xb);
+  a.Xn = (V2*)(k % 2 == 0 ? xb : xa);
+  if (c->lo > 0)
+    k_implicit_iter<NC, R, true><<<impl_grid(c), dim3(64, 3), 0, c->stream>>>(a);
+  else
+    k_implicit_iter<NC, R, false><<<impl_grid(c), dim3(64, 3), 0, c->stream>>>(a);
+  int st = cuda_check(cudaGetLastError(), "k_implicit_iter launch");
+  if (st || c->lo == 0) return st;
+  k_implicit_iter_halo<NC, R><<<(unsigned)((c->g.nxy + 63) / 64), 64, 0, c->stream>>>(a);
+  return cuda_check(cudaGetLastError(), "k_implicit_iter_halo launch");
+}
+
+// After `done` sweeps: the last iterate becomes U(t_{n+1}), U(t_n) becomes
+// U(t_{n-1}), and the old U(t_{n-1}) and the spare iterate buffer are reused.
+void implicit_commit(glasma_ctx* c, int done) {
+  void* prev = c->Uprev;
+  void* now = c->U[c->cur];
+  void* xa = c->U[1 - c->cur];
+  void* xb = c->Uit;
+  // iteration k writes xb for even k and xa for odd k
+  void* fin = ((done - 1) % 2 == 0) ? xb : xa;
+  void* spare = fin == xa ? xb : xa;
+  c->Uprev = now;
+  c->U[c->cur] = fin;
+  c->U[1 - c->cur] = prev;
+  c->Uit = spare;
+}
+
+template <int NC, typename R>
+static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
+  int st = implicit_prepare<NC, R>(c, hop);
   if (st) return st;
+  const int maxit = c->p.implicit_max_iter;
   for (int k = 0; k < maxit; ++k) {
-    a.k = k;
-    a.X = (const V2*)(k % 2 == 0 ? xa : xb);
-    a.Xn = (V2*)(k % 2 == 0 ? xb : xa);
-    k_implicit_iter<NC, R><<<gridz, bs, 0, c->stream>>>(a);
-    st = cuda_check(cudaGetLastError(), "k_implicit_iter launch");
+    st = implicit_launch_sweep<NC, R>(c, hop, k, true);
     if (st) return st;
   }
   std::vector<double> conv(2 * (maxit + 1));
@@ -362,21 +468,36 @@ static int implicit_t(glasma_ctx* c, bool hop, int* iters) {
   for (int k = 0; k < maxit; ++k) {
     done = k + 1;
     if (!isfinite(conv[k])) return set_error(GLASMA_ERR_NONFINITE, "implicit iteration met a non-finite value");
-    if (implicit_converged(conv.data(), maxit, k, a.tol, sizeof(R) == 4)) {
+    if (implicit_converged(conv.data(), maxit, k, c->p.implicit_tol, sizeof(R) == 4)) {
       converged = true;
       break;
     }
   }
   *iters = done;
-  // iteration k writes xb for even k and xa for odd k
-  void* fin = ((done - 1) % 2 == 0) ? xb : xa;
-  void* spare = fin == xa ? xb : xa;
-  c->Uprev = now;
-  c->U[c->cur] = fin;
-  c->U[1 - c->cur] = prev;
-  c->Uit = spare;
+  implicit_commit(c, done);
   if (!converged)
     return set_error(GLASMA_ERR_NOT_CONVERGED, "implicit iteration did not reach implicit_tol within implicit_max_iter");
+  return GLASMA_OK;
+}
+
+template <int NC, typename R>
+static int implicit_sweep_t(glasma_ctx* c, double* dmax, double* emax) {
+  const int k = c->impl_k;
+  int st = implicit_launch_sweep<NC, R>(c, c->impl_hop, k, false);
+  if (st) return st;
+  double h[2];
+  const int maxit = c->p.implicit_max_iter;
+  st = cuda_check(cudaMemcpyAsync(&h[0], c->conv + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                  "sweep maximum readback");
+  if (!st)
+    st = cuda_check(cudaMemcpyAsync(&h[1], c->conv + maxit + 1 + k, sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream),
+                    "sweep maximum readback");
+  if (!st) st = cuda_check(cudaStreamSynchronize(c->stream), "sweep sync");
+  if (st) return st;
+  c->impl_k = k + 1;
+  *dmax = h[0];
+  *emax = h[1];
   return GLASMA_OK;
 }
 
@@ -401,6 +522,17 @@ namespace glasma {
 int launch_step_implicit(glasma_ctx* c, bool hop, int* iters) {
   if (c->p.nc == 2) return c->rs == 8 ? implicit_t<2, double>(c, hop, iters) : implicit_t<2, float>(c, hop, iters);
   return c->rs == 8 ? implicit_t<3, double>(c, hop, iters) : implicit_t<3, float>(c, hop, iters);
+}
+
+int implicit_begin(glasma_ctx* c, bool hop) {
+  if (c->p.nc == 2) return c->rs == 8 ? implicit_prepare<2, double>(c, hop) : implicit_prepare<2, float>(c, hop);
+  return c->rs == 8 ? implicit_prepare<3, double>(c, hop) : implicit_prepare<3, float>(c, hop);
+}
+
+int implicit_sweep(glasma_ctx* c, double* dmax, double* emax) {
+  if (c->p.nc == 2)
+    return c->rs == 8 ? implicit_sweep_t<2, double>(c, dmax, emax) : implicit_sweep_t<2, float>(c, dmax, emax);
+  return c->rs == 8 ? implicit_sweep_t<3, double>(c, dmax, emax) : implicit_sweep_t<3, float>(c, dmax, emax);
 }
 
 }  // namespace glasma

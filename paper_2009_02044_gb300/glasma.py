@@ -105,6 +105,9 @@ def load_library(path=LIB_PATH):
                                                 C.POINTER(C.c_size_t)]),
         "glasma_slab_pack": (C.c_int, [P, C.c_int, P]),
         "glasma_slab_unpack": (C.c_int, [P, C.c_int, P]),
+        "glasma_implicit_begin": (C.c_int, [P]),
+        "glasma_implicit_sweep": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "glasma_implicit_end": (C.c_int, [P]),
         "glasma_gauss_residual_static": (
             C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                       C.c_double, C.c_double, P, P, P, C.c_int, C.c_int, P,
@@ -414,6 +417,24 @@ def glasma_slab_unpack(h, direction, dev_ptr):
     _check(load_library().glasma_slab_unpack(h.ptr, int(direction),
                                              C.c_void_p(dev_ptr)),
            "glasma_slab_unpack")
+
+
+def glasma_implicit_begin(h):
+    """Begin an improved step driven sweep by sweep (see include/glasma.h)."""
+    _check(load_library().glasma_implicit_begin(h.ptr), "glasma_implicit_begin")
+
+
+def glasma_implicit_sweep(h):
+    """One sweep; returns (max |dE|, max |E|) over the owned slices."""
+    d, e = C.c_double(), C.c_double()
+    _check(load_library().glasma_implicit_sweep(h.ptr, C.byref(d), C.byref(e)),
+           "glasma_implicit_sweep")
+    return d.value, e.value
+
+
+def glasma_implicit_end(h):
+    """Commit the step begun by glasma_implicit_begin."""
+    _check(load_library().glasma_implicit_end(h.ptr), "glasma_implicit_end")
 
 
 def glasma_free(h):

@@ -10,6 +10,13 @@ in rank order: the T^{mu nu}(z) rows of the owned slices, summed in z order
 for the total energy exactly as a single context sums them, and the Gauss
 residual maxima.
 
+Under the improved scheme (Sec. 3, Fig. wilson (b)) a step is the same
+exchange, then glasma_implicit_begin, sweeps whose maxima (the largest
+change of E and the largest E over the owned slices) are folded with max
+across the ranks before the stopping rule (glasma_implicit_converged), and
+glasma_implicit_end: every rank takes the sweeps the whole lattice would.
+The sweeps exchange nothing else.
+
 Transports: `DistTransport` sends the messages with torch.distributed
 point-to-point calls (NCCL between GPUs, gloo between CPU processes) and
 bounds every wait; a message that does not arrive in time ends the exchange
@@ -21,6 +28,7 @@ another rank: the exchange happens on the host between launches.
 from __future__ import annotations
 
 import datetime
+import math
 
 from . import glasma as G
 
@@ -47,6 +55,10 @@ class SlabRank:
         z0, z1 = slab_bounds(cfg["nz"], nranks)[self.rank]
         self.h = G.glasma_slab_init(cfg, z0, z1, rho, stream)
         self.z0, self.z1 = z0, z1
+        p = G.make_params(cfg)
+        self.implicit = p.scheme == G.IMPLICIT
+        self.tol, self.maxit = p.implicit_tol, p.implicit_max_iter
+        self.precision = "fp32" if p.precision == G.FP32 else "fp64"
         dev = device if device is not None else torch.cuda.current_device()
         self.buf = {}
         for d in (+1, -1):
@@ -83,6 +95,37 @@ class SlabRank:
 
     def tmunu_rows(self):
         return G.glasma_tmunu(self.h)[0]
+
+
+def implicit_step(ranks, fold):
+    """One improved step of the ranks this process holds, their halos
+    already exchanged: begin, sweeps until the stopping rule holds on the
+    maxima folded over all ranks by fold([(dmax, emax), ...]) -> (dmax,
+    emax), end.  Returns the number of sweeps."""
+    for r in ranks:
+        G.glasma_implicit_begin(r.h)
+    r0 = ranks[0]
+    dm, em = [], []
+    converged = False
+    for _ in range(r0.maxit):
+        d, e = fold([G.glasma_implicit_sweep(r.h) for r in ranks])
+        dm.append(d)
+        em.append(e)
+        if not math.isfinite(d):
+            raise G.GlasmaError(-4, "implicit_step", "a sweep met a non-finite value")
+        if G.glasma_implicit_converged(dm, em, r0.tol, r0.precision):
+            converged = True
+            break
+    for r in ranks:
+        G.glasma_implicit_end(r.h)
+    if not converged:
+        raise G.GlasmaError(-6, "implicit_step",
+                            "no convergence within %d sweeps" % r0.maxit)
+    return len(dm)
+
+
+def _fold_max(pairs):
+    return max(p[0] for p in pairs), max(p[1] for p in pairs)
 
 
 def merge_windows(all_windows):
@@ -134,6 +177,8 @@ class LocalTransport:
 
     def step(self):
         self.exchange()
+        if self.ranks[0].implicit:
+            return implicit_step(self.ranks, _fold_max)
         for r in self.ranks:
             r.step()
 
@@ -206,6 +251,17 @@ class DistTransport:
                           self.group)
         r.unpack()
 
+    def fold(self, pairs):
+        """Max over all ranks of this rank's (dmax, emax)."""
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend(self.group) == "nccl" else "cpu"
+        v = torch.tensor(list(pairs[0]), dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX, group=self.group)
+        return float(v[0]), float(v[1])
+
     def step(self):
         self.exchange()
+        if self.r.implicit:
+            return implicit_step([self.r], self.fold)
         self.r.step()

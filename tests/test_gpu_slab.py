@@ -113,8 +113,12 @@ def test_slab_calls_reject_bad_use(G):
         G.glasma_step(r.h, 1)
     with pytest.raises(G.GlasmaError):          # no rank below rank 0
         G.glasma_slab_pack(r.h, -1, r.buf[("send", +1)].data_ptr())
-    with pytest.raises(G.GlasmaError):
-        G.glasma_slab_init(dict(cfg, scheme="implicit"), 0, 20)
+    with pytest.raises(G.GlasmaError):          # improved scheme: sweep by sweep
+        ri = SL.SlabRank(dict(cfg, scheme="implicit"), 0, 2)
+        G.glasma_slab_set_windows(ri.h, *SL.merge_windows([ri.windows()]))
+        G.glasma_step(ri.h, 1)
+    with pytest.raises(G.GlasmaError):          # leapfrog context
+        G.glasma_implicit_begin(r.h)
     with pytest.raises(G.GlasmaError):
         G.glasma_slab_init(cfg, 20, 60)
     with pytest.raises(G.GlasmaError):          # checkpoints are whole lattices
@@ -122,3 +126,70 @@ def test_slab_calls_reject_bad_use(G):
     G.glasma_slab_set_windows(r.h, *SL.merge_windows([r.windows()]))
     with pytest.raises(G.GlasmaError):          # one step per exchange
         G.glasma_step(r.h, 2)
+
+
+# ---------------------------------------------------------------------------
+# The improved scheme on slabs (glasma_implicit_begin / _sweep / _end)
+# ---------------------------------------------------------------------------
+
+def _implicit_cfg(nc, precision, nz=47, nx=10, ny=12):
+    """a_z = 0.5, dt = 0.25 (a hop every other step); the nuclei meet after
+    20 steps and cross the slab boundaries."""
+    cfg = gi.small_config(nc, nz=nz, nx=nx, ny=ny, a_z=0.5, dt=0.25, sigma_l=1.0)
+    cfg.update(scheme="implicit", implicit_max_iter=60, precision=precision,
+               implicit_tol=1e-14 if precision == "fp64" else 1e-7)
+    return cfg
+
+
+@pytest.mark.parametrize("nc,precision", [(2, "fp64"), (3, "fp64"), (2, "fp32"), (3, "fp32")])
+@pytest.mark.parametrize("nranks", [2, 3])
+def test_implicit_slabs_match_the_whole_lattice(G, nc, precision, nranks):
+    """The improved scheme on 2 and 3 slabs of the ragged 47 x 10 x 12
+    collision for 30 steps, against one whole-lattice context (glasma_step,
+    all sweeps queued at once): the same sweeps every step, and the owned
+    slices, the T^{mu nu} rows, H and the Gauss residual maximum bit for
+    bit."""
+    from paper_2009_02044_gb300 import slab as SL
+    cfg = _implicit_cfg(nc, precision)
+    whole = G.glasma_init_mv(cfg, None)
+    ranks = [SL.SlabRank(cfg, r, nranks) for r in range(nranks)]
+    T = SL.LocalTransport(ranks)
+    T.setup()
+    for _ in range(30):
+        sweeps = T.step()
+        G.glasma_step(whole, 1)
+        assert sweeps == G.glasma_get_info(whole).implicit_iters
+        assert all(G.glasma_get_info(r.h).implicit_iters == sweeps for r in ranks)
+    T.exchange()
+    _compare(G, cfg, whole, ranks, T)
+    for r in ranks:
+        G.glasma_free(r.h)
+    G.glasma_free(whole)
+
+
+def test_implicit_sweeps_one_by_one_on_a_whole_lattice(G):
+    """glasma_implicit_begin / _sweep / _end on an ordinary context equals
+    glasma_step bit for bit (the host applies the same stopping rule)."""
+    from paper_2009_02044_gb300 import slab as SL
+    cfg = _implicit_cfg(3, "fp32", nz=40)
+    a = G.glasma_init_mv(cfg, None)
+    b = G.glasma_init_mv(cfg, None)
+    r = SL.SlabRank.__new__(SL.SlabRank)
+    r.h, r.tol, r.maxit, r.precision = b, cfg["implicit_tol"], cfg["implicit_max_iter"], "fp32"
+    for _ in range(12):
+        G.glasma_step(a, 1)
+        assert SL.implicit_step([r], SL._fold_max) == G.glasma_get_info(a).implicit_iters
+    fa, fb = G.glasma_get_fields(a), G.glasma_get_fields(b)
+    for x, y in zip(fa[:4], fb[:4]):
+        assert np.array_equal(x, y)
+    with pytest.raises(G.GlasmaError):          # a sweep before begin
+        G.glasma_implicit_sweep(b)
+    with pytest.raises(G.GlasmaError):          # end without a step
+        G.glasma_implicit_end(b)
+    G.glasma_implicit_begin(b)
+    with pytest.raises(G.GlasmaError):          # glasma_step while one is open
+        G.glasma_step(b, 1)
+    with pytest.raises(G.GlasmaError):          # no sweep done yet
+        G.glasma_implicit_end(b)
+    G.glasma_free(a)
+    G.glasma_free(b)
