@@ -813,7 +813,58 @@ def run_slab(G, torch, stream, cfg, nranks=(2, 4), steps=100, warm=5):
                                          and SL.total_energy(cfg, rows) == H_w)}
         for r in ranks:
             G.glasma_free(r.h)
+    out["improved"] = run_slab_improved(G, torch, stream)
     return out
+
+
+def run_slab_improved(G, torch, stream, nt=32, P=2, steps=10, warm=3):
+    """The improved-scheme workload (SU(3), 2048 slices, a_z = dt = a_T/4,
+    FP32), cut to nt x nt transversally, on P slabs of one GPU driven sweep
+    by sweep (glasma_implicit_*: each sweep's maxima read back and folded
+    across the slabs before the stopping rule) against the whole lattice's
+    glasma_step (every sweep queued at once): ms per step, sweeps per step,
+    and whether rows and H agree bit for bit."""
+    from paper_2009_02044_gb300 import slab as SL
+    cfg = dict(gi.CONFIGS["su3_2048x128x128_improved"], nx=nt, ny=nt, precision="fp32")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        whole = G.glasma_init_mv(cfg, None, stream=stream)
+        G.glasma_step(whole, warm)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        its_w = []
+        for _ in range(steps):
+            G.glasma_step(whole, 1)
+            its_w.append(G.glasma_get_info(whole).implicit_iters)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_w = ev0.elapsed_time(ev1)
+        tab_w, H_w = G.glasma_tmunu(whole)
+        G.glasma_free(whole)
+        ranks = [SL.SlabRank(cfg, r, P, stream=stream) for r in range(P)]
+        T = SL.LocalTransport(ranks)
+        T.setup()
+        for _ in range(warm):
+            T.step()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        its_s = [T.step() for _ in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = ev0.elapsed_time(ev1)
+        T.exchange()
+        rows = T.gather_rows()
+    for r in ranks:
+        G.glasma_free(r.h)
+    return {"workload": "su3_2048x128x128_improved cut to %dx%d, FP32" % (nt, nt),
+            "slabs": P, "steps_timed": steps,
+            "whole_ms_per_step": ms_w / steps, "slabs_ms_per_step": ms_s / steps,
+            "over_whole": ms_s / ms_w,
+            "sweeps_per_step": sum(its_s) / steps,
+            "same_sweeps": its_s == its_w,
+            "equals_whole_lattice": bool(np.array_equal(rows, tab_w)
+                                         and SL.total_energy(cfg, rows) == H_w)}
 
 
 def run_improved_error(G, torch, nt=16, steps=1000, every=50):
