@@ -204,3 +204,69 @@ def test_set_step_kernel_rejects_bad_arguments(G):
         G.glasma_set_step_kernel(wide, "plaquette")
     G.glasma_set_step_kernel(wide, "auto")
     G.glasma_step(wide, 2)            # auto falls back to the staple kernel
+
+
+# Degenerate transverse planes: one site (every transverse neighbour is the
+# site itself, each transverse plaquette of a 1-site direction is trivial),
+# one row, one column; the shortest box a placeholder event fits (nz = 5).
+DEGENERATE = [(5, 1, 1), (5, 1, 2), (6, 2, 1), (5, 3, 1)]
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+@pytest.mark.parametrize("shape", DEGENERATE)
+def test_degenerate_planes_match_oracle(G, nc, shape):
+    """Every kernel form in FP64 (1e-11) and FP32 (the bound of the FP32
+    random-state test), plus T^{mu nu} and the Gauss residual in FP64."""
+    nz, ny, nx = shape
+    st = _random_state(nc, nz, ny, nx, seed=3 * nz + 5 * ny + nx + nc)
+    st.QA[:] = 0.0
+    st.QB[:] = 0.0
+    st.QA[3] = 0.1
+    st.QB[1] = -0.1
+    ref = O.step(st, 3)
+    rtab, _ = O.tmunu(ref)
+    og = O.gauss_residual(ref)
+    for precision, kernels, tol in (("fp64", KERNELS, TOL64),
+                                    ("fp32", KERNELS + ["staple_pairs"], 1.5e-6)):
+        for kernel in kernels:
+            h = _ctx(G, st, precision)
+            G.glasma_set_step_kernel(h, kernel)
+            G.glasma_step(h, 3)
+            U, E, QA, QB, n = G.glasma_get_fields(h)
+            errs = dict(U=rel(U, ref.U), E=rel(E, ref.E), QA=rel(QA, ref.QA),
+                        QB=rel(QB, ref.QB))
+            assert all(v <= tol for v in errs.values()), (precision, kernel, errs)
+            if precision == "fp64":
+                tab, _ = G.glasma_tmunu(h)
+                assert rel(tab, rtab) <= TOL64, kernel
+                gm, _, rm = G.glasma_gauss_residual(h)
+                assert abs(gm - og[0]) <= 1e-12 * og[0] and abs(rm - og[2]) <= 1e-12 * og[2]
+            G.glasma_free(h)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_longest_lattice_matches_oracle(G, nc):
+    """nz = 65535, the most slices a context takes (one grid row per slice
+    in the step kernels), on a one-site plane: every kernel form, FP64."""
+    nz = 65535
+    st = _random_state(nc, nz, 1, 1, seed=11 + nc)
+    ref = O.step(st, 3)
+    rtab, _ = O.tmunu(ref)
+    for kernel in KERNELS:
+        h = _ctx(G, st)
+        G.glasma_set_step_kernel(h, kernel)
+        G.glasma_step(h, 3)
+        U, E, QA, QB, n = G.glasma_get_fields(h)
+        errs = dict(U=rel(U, ref.U), E=rel(E, ref.E), QA=rel(QA, ref.QA),
+                    QB=rel(QB, ref.QB))
+        assert all(v <= TOL64 for v in errs.values()), (kernel, errs)
+        tab, _ = G.glasma_tmunu(h)
+        assert rel(tab, rtab) <= TOL64, kernel
+        G.glasma_free(h)
+    # and the site-paired FP32 kernel (its grid runs over half the slices)
+    h = _ctx(G, st, "fp32")
+    G.glasma_set_step_kernel(h, "staple_pairs")
+    G.glasma_step(h, 3)
+    U, E, QA, QB, n = G.glasma_get_fields(h)
+    assert rel(U, ref.U) < 1.5e-6 and rel(E, ref.E) < 1.5e-6
+    G.glasma_free(h)
