@@ -838,25 +838,60 @@ class NotConverged(RuntimeError):
     pass
 
 
+# How the system is iterated (the paper says only that it is solved
+# iteratively; reading adopted here).  One sweep maps E to
+# G(E) = E(t_{n-1/2}) + dt J + dt F(exp(i dt E) U(t_n), U(t_n), U(t_{n-1})).
+# In the small-amplitude abelian limit its Jacobian is -w_0 dt^2 K', with
+# w_0 the weight of the slot t_{n+1} and K' the lattice curl-curl acting on
+# the links that take that slot: block triangular, with the curl-curl of
+# the (x, y) plane and the transverse Laplacian of A_z on its diagonal,
+# whose eigenvalues lie in [0, 8 / a_T^2].  So the eigenvalues of the sweep
+# lie in [-c, 0] with c = 8 w_0 dt^2 / a_T^2: the plain iteration
+# E <- G(E) contracts by c per sweep (c = 1/8 at dt = a_T/4) and diverges
+# for c >= 1.  Every sweep after the first is therefore relaxed,
+# E <- (1 - omega) E + omega G(E) with omega = 2 / (2 + c), which maps
+# [-c, 0] into [-c/(2+c), c/(2+c)]: the contraction is halved at small c
+# and stays below 1 for every dt.  The first sweep takes the full step
+# G(E(t_{n-1/2})), whose change is the bulk of the update.  The fixed point
+# is the same; weights (0, 1, 0) give omega = 1.
+def implicit_omega(p: Params, w=IMPLICIT_WEIGHTS):
+    """Relaxation of the sweeps after the first."""
+    c = 8.0 * w[0] * p.dt * p.dt / (p.a_t * p.a_t)
+    return 2.0 / (2.0 + c)
+
+
+def relax(Ek, G, omega):
+    """(1 - omega) Ek + omega G; exactly G when omega = 1."""
+    if omega == 1.0:
+        return G
+    return (1.0 - omega) * Ek + omega * G
+
+
 def step_implicit(st: State, n_steps=1, w=IMPLICIT_WEIGHTS, tol=1e-14,
-                  max_iter=100):
+                  max_iter=100, omega=None):
     """Semi-implicit steps: fixed-point iteration on E(t_{n+1/2}), starting
-    from U(t_{n+1}) = exp(i dt E(t_{n-1/2})) U(t_n), until the largest change
-    of any E component is below tol.  The CPIC hop and its current are the
-    leapfrog's (they use U(t_n) only).  U_prev must hold U(t_{n-1})."""
+    from U(t_{n+1}) = exp(i dt E(t_{n-1/2})) U(t_n), every sweep after the
+    first relaxed by omega (implicit_omega unless given), until the largest
+    change of any E component is below tol.  The CPIC hop and its current
+    are the leapfrog's (they use U(t_n) only).  U_prev must hold
+    U(t_{n-1})."""
     s = st.copy()
     p = s.p
+    om = implicit_omega(p, w) if omega is None else omega
     for _ in range(n_steps):
         QA, QB, djz = hop(s)
         Ek = s.E
         X = u_update(s.U, Ek, p)
+        deltas = []
         for it in range(max_iter):
             F = force_implicit((X, s.U, s.U_prev), p, w)
-            En = s.E + p.dt * F
-            En[2] = En[2] + djz
-            En[2] = np.where(link_mask(2, p.nz, p.ny, p.nx)[..., None],
-                             En[2], 0.0)
+            G = s.E + p.dt * F
+            G[2] = G[2] + djz
+            G[2] = np.where(link_mask(2, p.nz, p.ny, p.nx)[..., None],
+                            G[2], 0.0)
+            En = relax(Ek, G, 1.0 if it == 0 else om)
             delta = float(np.max(np.abs(En - Ek)))
+            deltas.append(delta)
             Ek = En
             X = u_update(s.U, En, p)
             if delta < tol:
@@ -864,5 +899,6 @@ def step_implicit(st: State, n_steps=1, w=IMPLICIT_WEIGHTS, tol=1e-14,
         else:
             raise NotConverged("implicit step did not converge")
         s.extra["iters"] = it + 1
+        s.extra["deltas"] = deltas
         s = State(p, X, Ek, QA, QB, s.n + 1, s.U, s.extra)
     return s

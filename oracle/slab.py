@@ -217,16 +217,18 @@ def implicit_begin(s: Slab):
     s.work = dict(QA=QA, QB=QB, djz=djz, Ek=st.E, X=O.u_update(st.U, st.E, st.p))
 
 
-def implicit_sweep(s: Slab, w=O.IMPLICIT_WEIGHTS):
-    """One sweep: E^(k+1) = E(t_{n-1/2}) + dt F(X^(k), U(t_n), U(t_{n-1}))
-    + dt J, X^(k+1) = exp(i dt E^(k+1)) U(t_n).  Returns the largest change
-    of E over the owned slices."""
+def implicit_sweep(s: Slab, k, w=O.IMPLICIT_WEIGHTS):
+    """Sweep k: G = E(t_{n-1/2}) + dt F(X^(k), U(t_n), U(t_{n-1})) + dt J,
+    E^(k+1) = G for k = 0 and relaxed towards G after
+    (oracle.glasma_oracle.implicit_omega), X^(k+1) = exp(i dt E^(k+1))
+    U(t_n).  Returns the largest change of E over the owned slices."""
     st, W = s.st, s.work
     p = st.p
     F = O.force_implicit((W["X"], st.U, st.U_prev), p, w)
-    En = st.E + p.dt * F
-    En[2] = En[2] + W["djz"]
-    En[2] = np.where(O.link_mask(2, p.nz, p.ny, p.nx)[..., None], En[2], 0.0)
+    G = st.E + p.dt * F
+    G[2] = G[2] + W["djz"]
+    G[2] = np.where(O.link_mask(2, p.nz, p.ny, p.nx)[..., None], G[2], 0.0)
+    En = O.relax(W["Ek"], G, 1.0 if k == 0 else O.implicit_omega(p, w))
     delta = float(np.max(np.abs(En - W["Ek"])[:, s.lo:s.hi]))
     W["Ek"] = En
     W["X"] = O.u_update(st.U, En, p)
@@ -254,7 +256,7 @@ def run_implicit_in_process(st: O.State, nranks, steps, w=O.IMPLICIT_WEIGHTS,
         for s in slabs:
             implicit_begin(s)
         for it in range(max_iter):
-            delta = max(implicit_sweep(s, w) for s in slabs)
+            delta = max(implicit_sweep(s, it, w) for s in slabs)
             if on_sweep:
                 on_sweep(slabs)
             if delta < tol:

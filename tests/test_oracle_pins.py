@@ -557,6 +557,50 @@ def test_implicit_dispersion_closed_form(case):
     assert w >= (kz / a_z if case != "kx_polz" else 0.0) - 1e-12
 
 
+def _transverse_mode_state(dt, a_z):
+    """U(1)-embedded E_z in the highest transverse mode, k_T = (pi, pi), on
+    the unit links: the eigenvector of the sweep's Jacobian with the
+    extreme eigenvalue -c, c = 8 w_0 dt^2 / a_T^2 (w_0 = 1/4)."""
+    p = O.Params(nc=2, nz=8, nx=4, ny=4, a_z=a_z, dt=dt)
+    Z, Y, X = _grid(p)
+    e3 = np.zeros((3,) + Z.shape)
+    e3[2] = 1e-6 * np.cos(np.pi * (X + Y))
+    e3[2][p.nz - 1] = 0.0
+    return _abelian_state(p, np.zeros((3,) + Z.shape), e3)
+
+
+@pytest.mark.parametrize("dt,a_z", [(0.25, 0.5), (0.5, 0.5)])
+def test_implicit_sweep_contraction_closed_form(dt, a_z):
+    """On the extreme transverse mode the plain iteration's changes shrink
+    by exactly c per sweep, the relaxed iteration's (omega = 2 / (2 + c)
+    after the first sweep) by c / (2 + c); both reach the same fixed
+    point."""
+    st = _transverse_mode_state(dt, a_z)
+    c = 8 * 0.25 * dt * dt
+    assert O.implicit_omega(st.p) == 2.0 / (2.0 + c)
+    plain = O.step_implicit(st, 1, tol=1e-19, omega=1.0)
+    relaxed = O.step_implicit(st, 1, tol=1e-19)
+    dp, dr = plain.extra["deltas"], relaxed.extra["deltas"]
+    rp = [dp[k + 1] / dp[k] for k in range(6)]
+    rr = [dr[k + 1] / dr[k] for k in range(1, 6)]
+    assert np.allclose(rp, c, rtol=1e-6), rp
+    assert np.allclose(rr, c / (2 + c), rtol=1e-6), rr
+    assert relaxed.extra["iters"] < plain.extra["iters"]
+    assert np.max(np.abs(relaxed.E - plain.E)) < 1e-18
+    assert np.max(np.abs(relaxed.U - plain.U)) < 1e-18
+
+
+def test_implicit_relaxed_iteration_converges_where_plain_fails():
+    """dt = a_T (c = 2): the plain iteration doubles its changes every sweep
+    and never settles; the relaxed one contracts by c / (2 + c) = 1/2."""
+    st = _transverse_mode_state(1.0, 1.0)
+    with pytest.raises(O.NotConverged):
+        O.step_implicit(st, 1, tol=1e-19, omega=1.0, max_iter=40)
+    s = O.step_implicit(st, 1, tol=1e-19, max_iter=80)
+    d = s.extra["deltas"]
+    assert np.allclose([d[k + 1] / d[k] for k in range(1, 6)], 0.5, rtol=1e-6)
+
+
 def test_implicit_abelian_gauss_is_conserved():
     """In the U(1) embedding each plane keeps one antisymmetric, time-averaged
     field strength, so the abelian Gauss law is conserved exactly."""

@@ -117,7 +117,7 @@ def test_uprev_halo_is_needed():
     for s in slabs:
         S.implicit_begin(s)
     for it in range(100):
-        if max(S.implicit_sweep(s) for s in slabs) < 1e-12:
+        if max(S.implicit_sweep(s, it) for s in slabs) < 1e-12:
             break
     for s in slabs:
         S.implicit_end(s, it + 1)
@@ -178,7 +178,7 @@ def _gloo_rank(rank, port, nc, steps, q):
         halo()
         S.implicit_begin(s)
         for it in range(100):
-            d = torch.tensor([S.implicit_sweep(s)], dtype=torch.float64)
+            d = torch.tensor([S.implicit_sweep(s, it)], dtype=torch.float64)
             dist.all_reduce(d, op=dist.ReduceOp.MAX)
             if float(d[0]) < 1e-13:
                 break
