@@ -466,6 +466,10 @@ GLASMA_API int glasma_implicit_converged(const double* dmax, const double* emax,
  *   its E as E(t_{n+1/2}), move the charge windows of a hop step, advance
  *   the step counter (glasma_get_info reports the sweeps).  Errors:
  *   INVALID_ARG (no step begun, no sweep done).
+ * Between _begin and _end the fields are mid-iteration: glasma_step, the
+ *   observables, field and checkpoint transfers and slab messages return
+ *   INVALID_ARG until _end.  A sweep that returns a non-finite maximum
+ *   leaves the step open and its state undefined.
  */
 GLASMA_API int glasma_implicit_begin(glasma_ctx* c);
 GLASMA_API int glasma_implicit_sweep(glasma_ctx* c, double* dmax, double* emax);

@@ -336,6 +336,14 @@ int glasma_step(glasma_ctx* c, int n_steps) {
   return GLASMA_OK;
 }
 
+// Between glasma_implicit_begin and _end the fields are mid-iteration (E is
+// iterated in place): calls that read or replace the state wait for _end.
+static int reject_open_step(const glasma_ctx* c) {
+  if (c->impl_active)
+    return set_error(GLASMA_ERR_INVALID_ARG, "an improved step is in progress (glasma_implicit_end first)");
+  return GLASMA_OK;
+}
+
 // exit checks of a hop step, in global slices (a slab's windows are the
 // whole lattice's)
 static int hop_exit_check(const glasma_ctx* c) {
@@ -390,6 +398,7 @@ int glasma_implicit_end(glasma_ctx* c) {
 
 int glasma_gauss_residual(glasma_ctx* c, double* max_abs, double* rms, double* rho_max) {
   if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   double r[3];
   int st = launch_gauss(c, r);
@@ -402,6 +411,7 @@ int glasma_gauss_residual(glasma_ctx* c, double* max_abs, double* rms, double* r
 
 int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total) {
   if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   const bool hop = hop_at(c->n, c->hop_p, c->hop_q);
   std::vector<double> tab(4 * (size_t)c->g.nz);
@@ -424,6 +434,7 @@ int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total) {
 int glasma_tmunu_device(glasma_ctx* c, double* dev_out) {
   if (!c || !dev_out) return set_error(GLASMA_ERR_INVALID_ARG, "context or dev_out is NULL");
   if (((uintptr_t)dev_out & 7) != 0) return set_error(GLASMA_ERR_INVALID_ARG, "dev_out must be 8-byte aligned");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   return launch_tmunu(c, hop_at(c->n, c->hop_p, c->hop_q), nullptr, dev_out);
 }
@@ -531,6 +542,7 @@ static int reals_to_dev(glasma_ctx* c, void* dev, const double* h, size_t n) {
 
 int glasma_get_fields(glasma_ctx* c, double* U, double* E, double* QA, double* QB, long long* step_n) {
   if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   const int64_t V = c->g.V, nxy = c->g.nxy;
   const int nc = c->p.nc, na = c->na, nv = c->nv;
@@ -622,6 +634,7 @@ int glasma_set_fields(glasma_ctx* c, const double* U, const double* E, const dou
                       const double* U_prev, long long step_n) {
   if (!c || !U || !E || step_n < 0) return set_error(GLASMA_ERR_INVALID_ARG, "bad context, U, E or step_n");
   if (c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "set_fields takes a whole lattice, not a slab");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   const int64_t V = c->g.V, nxy = c->g.nxy;
   const int na = c->na, nc = c->p.nc;
@@ -729,6 +742,7 @@ int glasma_state_bytes(const glasma_ctx* c, size_t* bytes) {
 
 int glasma_get_state(glasma_ctx* c, void* host_buf, size_t bytes) {
   if (c && c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "checkpoints hold whole lattices, not slabs");
+  if (c && reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   size_t need;
   int st = glasma_state_bytes(c, &need);
   if (st) return st;
@@ -777,6 +791,7 @@ int glasma_get_state(glasma_ctx* c, void* host_buf, size_t bytes) {
 int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes) {
   if (!c || !host_buf || bytes < sizeof(StateHeader)) return set_error(GLASMA_ERR_INVALID_ARG, "bad state buffer");
   if (c->slab) return set_error(GLASMA_ERR_INVALID_ARG, "checkpoints hold whole lattices, not slabs");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   StateHeader h;
   memcpy(&h, host_buf, sizeof(h));
@@ -926,6 +941,7 @@ int glasma_slab_pack(glasma_ctx* c, int dir, void* dev_buf) {
   if ((dir == 1 && c->hi == c->g.nz) || (dir == -1 && c->lo == 0))
     return set_error(GLASMA_ERR_INVALID_ARG, "no neighbouring slab in that direction");
   if (((uintptr_t)dev_buf & 15) != 0) return set_error(GLASMA_ERR_INVALID_ARG, "message buffer must be 16-byte aligned");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   return slab_pack(c, dir, dev_buf);
 }
@@ -935,6 +951,7 @@ int glasma_slab_unpack(glasma_ctx* c, int dir, const void* dev_buf) {
   if ((dir == 1 && c->hi == c->g.nz) || (dir == -1 && c->lo == 0))
     return set_error(GLASMA_ERR_INVALID_ARG, "no neighbouring slab in that direction");
   if (((uintptr_t)dev_buf & 15) != 0) return set_error(GLASMA_ERR_INVALID_ARG, "message buffer must be 16-byte aligned");
+  if (reject_open_step(c)) return GLASMA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   return slab_unpack(c, dir, dev_buf);
 }

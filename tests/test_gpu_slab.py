@@ -189,6 +189,10 @@ def test_implicit_sweeps_one_by_one_on_a_whole_lattice(G):
     G.glasma_implicit_begin(b)
     with pytest.raises(G.GlasmaError):          # glasma_step while one is open
         G.glasma_step(b, 1)
+    with pytest.raises(G.GlasmaError):          # observables wait for _end
+        G.glasma_tmunu(b)
+    with pytest.raises(G.GlasmaError):          # and so do transfers
+        G.glasma_get_fields(b)
     with pytest.raises(G.GlasmaError):          # no sweep done yet
         G.glasma_implicit_end(b)
     G.glasma_free(a)
