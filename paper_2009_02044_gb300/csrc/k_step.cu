@@ -6,17 +6,26 @@
 
 namespace glasma {
 
-// One thread per link.  A block is 64 consecutive transverse sites times the
-// three directions (threadIdx.y = direction), so the three link updates of a
-// site run together and share the neighbour links in L1; blockIdx.y is the
-// z slice.  A thread holds the staple sum and one neighbour product at a
-// time and reloads its own link after the staples (fewer live registers).
-// FP32: 3 blocks of 192 threads per SM; FP64 needs twice the registers.
-template <typename R> struct StepOcc { static constexpr int blocks = 3; };
-template <> struct StepOcc<double> { static constexpr int blocks = 1; };
+// One thread per link.  A block is `sites` consecutive transverse sites
+// times the three directions (threadIdx.y = direction), so the three link
+// updates of a site run together and share the neighbour links in L1;
+// blockIdx.y is the z slice.  A thread holds the staple sum and one
+// neighbour product at a time and reloads its own link after the staples
+// (fewer live registers).  FP32: 6 blocks of 32 sites (96 threads) per SM,
+// 18 warps at 96 registers (at most 5 warps on each of the 4 schedulers);
+// 15 warps at 126 registers without spills, or 12, were slower.  FP64
+// needs twice the registers.
+template <typename R> struct StepOcc {
+  static constexpr int blocks = 6;
+  static constexpr int sites = 32;
+};
+template <> struct StepOcc<double> {
+  static constexpr int blocks = 1;
+  static constexpr int sites = 64;
+};
 
 template <int NC, typename R>
-__global__ void __launch_bounds__(192, StepOcc<R>::blocks) k_step_leapfrog(StepArgs<R> a) {
+__global__ void __launch_bounds__(3 * StepOcc<R>::sites, StepOcc<R>::blocks) k_step_leapfrog(StepArgs<R> a) {
   step_link<NC, R>(a, (int)threadIdx.y, blockIdx.x * blockDim.x + threadIdx.x, (int)blockIdx.y + a.zlo);
 }
 
@@ -40,7 +49,7 @@ static int launch_t(glasma_ctx* c, bool hop) {
   a.zB0 = c->zB0;
   a.WB = c->WB;
   a.zlo = c->lo;
-  const int bs = 64;
+  const int bs = StepOcc<R>::sites;
   const unsigned ntb = (unsigned)((c->g.nxy + bs - 1) / bs);
   k_step_leapfrog<NC, R><<<dim3(ntb, (unsigned)(c->hi - c->lo)), dim3(bs, 3), 0, c->stream>>>(a);
   return cuda_check(cudaGetLastError(), "k_step_leapfrog launch");
