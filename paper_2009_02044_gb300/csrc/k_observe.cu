@@ -183,6 +183,11 @@ struct TmnArgs {
   R w[3];
   R az2;
   double a[3];
+  // products of reciprocals of the spacings, formed on the host (an FP64
+  // division is a long sequence on GB300's narrow FP64 pipe):
+  double binv[3];   // 1 / (a_i a_j)^2 of the planes xy, xz, yz
+  double hinv2[3];  // 1 / (2 a_i^2)
+  double slc[2];    // Poynting weights 1 / (a_x^2 a_z), 1 / (a_y^2 a_z)
   int hop;
   int zA0, WA, zB0, WB;
   int split;     // blocks per z slice
@@ -190,16 +195,19 @@ struct TmnArgs {
 };
 
 // ||x - y||_F^2 of two links in the state's representation (for FP32 the
-// deviations from 1, whose difference is that of the links), each entry's
-// difference formed in FP64 (exact for FP32 entries).
+// deviations from 1, whose difference is that of the links), in the state's
+// precision: a difference of two FP32 entries rounds to within u of itself,
+// and the sum of squares has no cancellation, so the FP32 value carries the
+// FP32 products' own relative accuracy; it enters the FP64 sums once per
+// site.
 template <int NC, typename R> struct Fro2;
 template <typename R>
 struct Fro2<3, R> {
-  GL_HD static double diff(const typename Group<3, R>::M& x, const typename Group<3, R>::M& y) {
-    double acc = 0.0;
+  GL_HD static R diff(const typename Group<3, R>::M& x, const typename Group<3, R>::M& y) {
+    R acc = R(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const double dr = (double)x.m[k].re - (double)y.m[k].re, di = (double)x.m[k].im - (double)y.m[k].im;
+      const R dr = x.m[k].re - y.m[k].re, di = x.m[k].im - y.m[k].im;
       acc += dr * dr + di * di;
     }
     return acc;
@@ -207,16 +215,18 @@ struct Fro2<3, R> {
 };
 template <typename R>
 struct Fro2<2, R> {
-  GL_HD static double diff(const typename Group<2, R>::M& x, const typename Group<2, R>::M& y) {
-    const double a = (double)x.a.re - (double)y.a.re, b = (double)x.a.im - (double)y.a.im;
-    const double c = (double)x.b.re - (double)y.b.re, d = (double)x.b.im - (double)y.b.im;
-    return 2.0 * (a * a + b * b + c * c + d * d);
+  GL_HD static R diff(const typename Group<2, R>::M& x, const typename Group<2, R>::M& y) {
+    const R a = x.a.re - y.a.re, b = x.a.im - y.a.im;
+    const R c = x.b.re - y.b.re, d = x.b.im - y.b.im;
+    return R(2) * (a * a + b * b + c * c + d * d);
   }
 };
 
 // Per-site arithmetic in the state's precision R (so E(n+1/2) equals what
 // the step kernel would write; FP32 plaquette products in the deviation
-// form), every accumulation in FP64.  Block (iz, p) takes the sites
+// form; the per-site sums of squares and of E B products in R, all of
+// positive terms except the Poynting sum), every accumulation over sites in
+// FP64.  Block (iz, p) takes the sites
 // t = p*256 + threadIdx.x + k*split*256 of slice iz; k_tmunu_fold adds the
 // split block sums of a slice in a fixed order.
 template <int NC, typename R>
@@ -245,16 +255,16 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
     {
       const M A = G::mul(IO::template load<R>(a.U, 0, a.g.V, s), IO::template load<R>(a.U, 1, a.g.V, n.p[0]));
       const M B = G::mul(IO::template load<R>(a.U, 1, a.g.V, s), IO::template load<R>(a.U, 0, a.g.V, n.p[1]));
-      bxy = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[1] * a.a[0] * a.a[1]);
+      bxy = (double)Fro2<NC, R>::diff(A, B) * a.binv[0];
     }
     if (iz <= a.g.nz - 2) {
       M A = G::mul(IO::template load<R>(a.U, 0, a.g.V, s), IO::template load<R>(a.U, 2, a.g.V, n.p[0]));  // U_x U_z(x+x)
       M B = G::mul(IO::template load<R>(a.U, 2, a.g.V, s), IO::template load<R>(a.U, 0, a.g.V, n.p[2]));  // U_z U_x(x+z)
-      bxz = Fro2<NC, R>::diff(A, B) / (a.a[0] * a.a[2] * a.a[0] * a.a[2]);
+      bxz = (double)Fro2<NC, R>::diff(A, B) * a.binv[1];
       Group<NC, R>::proj(G::mul_d(A, B), pry);  // B_y = -2 Im tr t U_zx / (a_z a_x) = +2 Im tr t U_xz / (a_x a_z)
       A = G::mul(IO::template load<R>(a.U, 1, a.g.V, s), IO::template load<R>(a.U, 2, a.g.V, n.p[1]));  // U_y U_z(x+y)
       B = G::mul(IO::template load<R>(a.U, 2, a.g.V, s), IO::template load<R>(a.U, 1, a.g.V, n.p[2]));  // U_z U_y(x+z)
-      byz = Fro2<NC, R>::diff(A, B) / (a.a[1] * a.a[2] * a.a[1] * a.a[2]);
+      byz = (double)Fro2<NC, R>::diff(A, B) * a.binv[2];
       Group<NC, R>::proj(G::mul_d(A, B), prx);  // B_x = -2 Im tr t U_yz / (a_y a_z)
     }
     double e2[3] = {0, 0, 0};
@@ -289,16 +299,18 @@ __global__ void __launch_bounds__(kRedThreads) k_tmunu(TmnArgs<R> a) {
 #pragma unroll
         for (int c = 0; c < NA; ++c) en[c] += dj[c];
       }
-      double acc = 0;
+      R acc = R(0), dot = R(0);
 #pragma unroll
       for (int c = 0; c < NA; ++c) {
-        double o = (double)eo[c], nn = (double)en[c];
+        const R o = eo[c], nn = en[c];
         acc += o * o + nn * nn;
-        // S_L = sum_a (Ebar_x B_y - Ebar_y B_x), Ebar the time mean of E / a
-        if (i == 0) s_l += 0.5 * (o + nn) / a.a[0] * (2.0 * (double)pry[c] / (a.a[0] * a.a[2]));
-        if (i == 1) s_l -= 0.5 * (o + nn) / a.a[1] * (-2.0 * (double)prx[c] / (a.a[1] * a.a[2]));
+        // S_L = sum_a (Ebar_x B_y - Ebar_y B_x), Ebar the time mean of E / a,
+        // B_y = 2 pry / (a_x a_z), B_x = -2 prx / (a_y a_z)
+        if (i == 0) dot += (o + nn) * pry[c];
+        if (i == 1) dot += (o + nn) * prx[c];
       }
-      e2[i] = 0.5 * acc / (a.a[i] * a.a[i]);
+      if (i < 2) s_l += a.slc[i] * (double)dot;
+      e2[i] = (double)acc * a.hinv2[i];
     }
     double e = 0.5 * (e2[0] + e2[1] + e2[2]) + bxy + bxz + byz;
     double p_t = 0.5 * e2[2] + bxy;
@@ -348,6 +360,12 @@ static int tmunu_t(glasma_ctx* c, bool hop, double* host_tab, double* dev_tab) {
   a.az2 = (R)(c->p.a_z * c->p.a_z);
   a.a[0] = a.a[1] = c->p.a_t;
   a.a[2] = c->p.a_z;
+  a.binv[0] = 1.0 / (a.a[0] * a.a[1] * a.a[0] * a.a[1]);
+  a.binv[1] = 1.0 / (a.a[0] * a.a[2] * a.a[0] * a.a[2]);
+  a.binv[2] = 1.0 / (a.a[1] * a.a[2] * a.a[1] * a.a[2]);
+  for (int i = 0; i < 3; ++i) a.hinv2[i] = 0.5 / (a.a[i] * a.a[i]);
+  a.slc[0] = 1.0 / (a.a[0] * a.a[0] * a.a[2]);
+  a.slc[1] = 1.0 / (a.a[1] * a.a[1] * a.a[2]);
   a.hop = hop ? 1 : 0;
   a.zA0 = c->zA0;
   a.WA = c->WA;
