@@ -504,10 +504,11 @@ GLASMA_API int glasma_adjoint_energy(const glasma_params* p, const double* rho_h
  * independent leapfrog events, possibly of different nz, ny, nx, advanced
  * together.  Each event's result is bitwise the one glasma_step gives it
  * alone (the same per-link arithmetic).  Execution modes:
- *   GLASMA_BATCH_GRAPH (default): one batched kernel launch per time step
- *     over all events' work; the launches of one call are captured on a
- *     private stream into one CUDA graph, launched on the events' stream.
- *     The call does not synchronise.
+ *   GLASMA_BATCH_GRAPH (default): per time step, one kernel launch per
+ *     geometry class (the events of equal nz, ny, nx together); the
+ *     launches of one call are captured on a private stream into one CUDA
+ *     graph, launched on the events' stream.  The call does not
+ *     synchronise.
  *   GLASMA_BATCH_PERSISTENT: one cooperative launch per 64 steps, its
  *     blocks resident throughout and meeting at a grid barrier between
  *     steps.  Every barrier wait is bounded (glasma_batch_set_barrier); a
