@@ -216,7 +216,8 @@ def exchange_messages(send, recv, rank, nranks, timeout_s=30.0, group=None):
 
 
 class DistTransport:
-    """One slab per process; messages through torch.distributed."""
+    """One slab per process; messages through torch.distributed: device
+    buffers with NCCL, staged through host memory with gloo."""
 
     def __init__(self, rank_obj, timeout_s=30.0, group=None):
         self.r = rank_obj
@@ -242,13 +243,23 @@ class DistTransport:
 
     def exchange(self):
         import torch
+        import torch.distributed as dist
         r = self.r
         r.pack()
         torch.cuda.synchronize()
-        send = {d: r.buf[("send", d)] for d in (+1, -1) if r.has(d)}
-        recv = {d: r.buf[("recv", d)] for d in (+1, -1) if r.has(d)}
+        keys = [d for d in (+1, -1) if r.has(d)]
+        if dist.get_backend(self.group) == "nccl":
+            send = {d: r.buf[("send", d)] for d in keys}
+            recv = {d: r.buf[("recv", d)] for d in keys}
+        else:
+            # gloo moves host tensors: the messages go through host memory
+            send = {d: r.buf[("send", d)].cpu() for d in keys}
+            recv = {d: torch.empty(r.buf[("recv", d)].shape, dtype=torch.uint8) for d in keys}
         exchange_messages(send, recv, r.rank, r.nranks, self.timeout_s,
                           self.group)
+        for d in keys:
+            if recv[d] is not r.buf[("recv", d)]:
+                r.buf[("recv", d)].copy_(recv[d])
         r.unpack()
 
     def fold(self, pairs):

@@ -197,3 +197,73 @@ def test_implicit_sweeps_one_by_one_on_a_whole_lattice(G):
         G.glasma_implicit_end(b)
     G.glasma_free(a)
     G.glasma_free(b)
+
+
+# ---------------------------------------------------------------------------
+# Two processes, one slab each, exchanging through torch.distributed (gloo,
+# messages staged through host memory; NCCL needs one GPU per rank)
+# ---------------------------------------------------------------------------
+
+def _dist_rank(rank, port, cfg, steps, q):
+    import datetime
+    import os
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=2,
+                            timeout=datetime.timedelta(seconds=120))
+    torch.cuda.set_device(0)
+    from paper_2009_02044_gb300 import glasma as G
+    from paper_2009_02044_gb300 import slab as SL
+    G.load_library()
+    r = SL.SlabRank(cfg, rank, 2)
+    T = SL.DistTransport(r, timeout_s=60.0)
+    T.setup()
+    sweeps = [T.step() for _ in range(steps)]
+    T.exchange()
+    rows = torch.from_numpy(np.ascontiguousarray(r.tmunu_rows()))
+    if rank == 1:
+        dist.send(rows, 0)
+    else:
+        n1 = SL.slab_bounds(cfg["nz"], 2)[1]
+        other = torch.empty((n1[1] - n1[0], 4), dtype=torch.float64)
+        dist.recv(other, 1)
+        all_rows = np.concatenate([rows.numpy(), other.numpy()])
+        whole = G.glasma_init_mv(cfg, None)
+        ws = []
+        for _ in range(steps):
+            G.glasma_step(whole, 1)
+            ws.append(G.glasma_get_info(whole).implicit_iters)
+        tab, H = G.glasma_tmunu(whole)
+        ok = bool(np.array_equal(all_rows, tab) and SL.total_energy(cfg, all_rows) == H)
+        if cfg.get("scheme") == "implicit":
+            ok = ok and sweeps == ws
+        q.put(ok)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("scheme", ["leapfrog", "implicit"])
+def test_two_processes_match_the_whole_lattice(G, scheme):
+    """Two processes on the one GPU, each with its slab context, stepping
+    through the collision with DistTransport: the gathered T^{mu nu} rows
+    and H equal one whole-lattice context's bit for bit (under the improved
+    scheme also the sweeps, folded with an allreduce every sweep)."""
+    import socket
+    import torch.multiprocessing as mp
+    if scheme == "implicit":
+        cfg = _implicit_cfg(3, "fp32")
+    else:
+        cfg = dict(gi.small_config(3, nz=47, sigma_l=2.0), precision="fp32")
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_dist_rank, args=(r, port, cfg, 30, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    assert all(p.exitcode == 0 for p in procs)
+    assert q.get(timeout=5) is True
