@@ -115,11 +115,10 @@ def step_kernel_hash():
 
 def step_kernel_name(nc, precision, kernel):
     """The CUDA kernel glasma_step launches for this choice (the library's
-    automatic choice: plaquette kernel in FP64, staple kernel on site pairs
-    for SU(2) FP32, one-site staple kernel for SU(3) FP32)."""
+    automatic choice: plaquette kernel in FP64, one-site staple kernel in
+    FP32)."""
     if kernel == "auto":
-        kernel = ("plaquette" if precision == "fp64" else
-                  "staple_pairs" if nc == 2 else "staple")
+        kernel = "plaquette" if precision == "fp64" else "staple"
     return {"staple": "k_step_leapfrog", "staple_pairs": "k_step_pair",
             "plaquette": "k_step_plaq", "plaquette_256": "k_step_plaq"}[kernel]
 

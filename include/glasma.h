@@ -97,7 +97,9 @@ typedef struct {
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
  * callbacks are called only from glasma_init_mv / glasma_free /
- * glasma_set_fields on the calling thread. */
+ * glasma_set_fields on the calling thread.  alloc must return 16-byte
+ * aligned memory (the state arrays are read with 16-byte vector loads);
+ * glasma_init_mv rejects anything else with GLASMA_ERR_INVALID_ARG. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* user);
   void (*free)(void* ptr, size_t bytes, void* stream, void* user);
@@ -195,9 +197,10 @@ GLASMA_API int glasma_tmunu_device(glasma_ctx* c, double* dev_out);
  * Inputs are device pointers in the library's layout (x fastest, site
  * s = (iz*ny + iy)*nx + ix, V = nz*ny*nx; R = double for GLASMA_FP64,
  * float for GLASMA_FP32):
- *   U  links, complex component k of link d at site s as (re, im) pairs
- *      of R.  SU(2): k = 0, 1 for (alpha, beta) of
- *      [[alpha, beta], [-beta*, alpha*]], at U[(d*2 + k)*V + s].
+ *   U  links (16-byte aligned), complex component k of link d at site s
+ *      as (re, im) pairs of R.  SU(2): k = 0, 1 for (alpha, beta) of
+ *      [[alpha, beta], [-beta*, alpha*]], at U[(d*V + s)*2 + k] (one
+ *      link's two pairs are adjacent).
  *      SU(3): k = 0..8 for the row-major 3x3 entries, in blocks of 32
  *      sites: U[((d*C + s/32)*9 + k)*32 + s%32] with C = ceil(V/32)
  *      (the array holds 3*9*32*C pairs; the padding is not read).
@@ -220,7 +223,8 @@ GLASMA_API int glasma_tmunu_device(glasma_ctx* c, double* dev_out);
  * must be serialised by the caller.  Work runs on `stream` (cudaStream_t,
  * NULL = legacy default); the call synchronises it and copies the result
  * to pageable host memory, so it cannot be recorded into a CUDA graph.
- * Errors: INVALID_ARG, NONFINITE, CUDA.
+ * Errors: INVALID_ARG (including a U that is not 16-byte aligned),
+ * NONFINITE, CUDA.
  */
 GLASMA_API int glasma_gauss_residual_static(int nc, int precision, int nz, int ny, int nx, double a_t,
                                             double a_z, const void* U, const void* E, const void* QA,
@@ -369,8 +373,7 @@ GLASMA_API int glasma_slab_unpack(glasma_ctx* c, int dir, const void* dev_buf);
  *                              row fits one block (nx <= 320; its 24% fewer
  *                              FMAs win where the FP64 pipe bounds the
  *                              step), else the staple kernel; for FP32 the
- *                              staple kernel (SU(3)) or the paired staple
- *                              kernel (SU(2)). */
+ *                              staple kernel. */
 enum { GLASMA_KERNEL_AUTO = 0, GLASMA_KERNEL_STAPLE = 1, GLASMA_KERNEL_PLAQUETTE = 2,
        GLASMA_KERNEL_PLAQUETTE_256 = 3, GLASMA_KERNEL_STAPLE_PAIRS = 4 };
 

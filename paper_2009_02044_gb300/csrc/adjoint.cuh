@@ -69,8 +69,8 @@ GL_HD Q4 q_from(const Group<2, double>::M& m) { return Q4{m.a.re, m.b.im, m.b.re
 
 // link d at site s of an FP64 SU(2) link array ((alpha, beta) as double2)
 GL_HD Q4 q_load(const double2* U, int d, int64_t V, int64_t s) {
-  const double2 a = U[(int64_t)(d * 2 + 0) * V + s];
-  const double2 b = U[(int64_t)(d * 2 + 1) * V + s];
+  const double2 a = U[link_index(2, d, 0, V, s)];
+  const double2 b = U[link_index(2, d, 1, V, s)];
   return Q4{a.x, b.y, b.x, a.y};
 }
 

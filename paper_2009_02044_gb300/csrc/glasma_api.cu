@@ -133,8 +133,9 @@ static int check_params(const glasma_params* p) {
 // 12.8 against 15.3 ms per SU(3) 512 x 64^2 step); in FP32 SU(3) the
 // one-site staple kernel (0.469 ms, against 0.521 for the plaquette kernel
 // and 0.572 for site pairs, whose 168 registers leave too few warps to hide
-// latency); in FP32 SU(2) site pairs (1.17 against 1.22 ms per
-// 1024 x 128^2 step).
+// latency); in FP32 SU(2) the staple kernel too (1.10 against 1.39 ms for
+// site pairs per 1024 x 128^2 step, once a link's alpha and beta became one
+// 16-byte load: the pairs' 32-bit loads then stride 16 bytes).
 bool use_plaq_kernel(const glasma_ctx* c) {
   if (c->step_kernel == GLASMA_KERNEL_PLAQUETTE || c->step_kernel == GLASMA_KERNEL_PLAQUETTE_256) return plaq_fits(c);
   return c->step_kernel == GLASMA_KERNEL_AUTO && c->rs == 8 && plaq_fits(c);
@@ -142,7 +143,7 @@ bool use_plaq_kernel(const glasma_ctx* c) {
 
 bool use_pair_kernel(const glasma_ctx* c) {
   if (c->rs != 4 || c->slab) return false;  // the pairs span the whole z range
-  return c->step_kernel == GLASMA_KERNEL_STAPLE_PAIRS || (c->step_kernel == GLASMA_KERNEL_AUTO && c->p.nc == 2);
+  return c->step_kernel == GLASMA_KERNEL_STAPLE_PAIRS;
 }
 
 int launch_step_chosen(glasma_ctx* c, bool hop) {
@@ -245,6 +246,15 @@ static int create_ctx(const glasma_params* p, const double* rho_host, void* stre
       (p->scheme == GLASMA_IMPLICIT && (!c->Uprev || !c->Uit || !c->Ework || !c->conv))) {
     glasma_free(c);
     return set_error(GLASMA_ERR_OOM, "state allocation failed");
+  }
+  {
+    // vector loads of links and fields need 16-byte aligned buffers
+    const void* need[6] = {c->U[0], c->U[1], c->E, c->Uprev, c->Uit, c->Ework};
+    for (int k = 0; k < 6; ++k)
+      if (((uintptr_t)need[k] & 15) != 0) {
+        glasma_free(c);
+        return set_error(GLASMA_ERR_INVALID_ARG, "the allocator must return 16-byte aligned memory");
+      }
   }
   if (link_elems(p->nc, c->g.V) != (int64_t)3 * c->nv * c->g.V) {
     // SU(3) pads the last block of 32 sites of each direction: zero it, so

@@ -151,7 +151,7 @@ StateRef alloc_state(Scratch& sc, const glasma_ctx* c) {
 __global__ void k_links_to64(const float2* in, double2* out, int64_t V) {
   GRID_STRIDE(i, 6 * V) {
     const float2 v = in[i];
-    const bool alpha = ((i / V) & 1) == 0;
+    const bool alpha = (i & 1) == 0;  // link_index(2, d, k, V, s) = (d V + s) 2 + k
     out[i] = make_double2((double)v.x + (alpha ? 1.0 : 0.0), (double)v.y);
   }
 }

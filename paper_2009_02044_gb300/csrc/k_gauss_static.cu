@@ -169,6 +169,7 @@ extern "C" GLASMA_API int glasma_gauss_residual_static(int nc, int precision, in
   if (nz < 1 || nx < 1 || ny < 1) return set_error(GLASMA_ERR_INVALID_ARG, "need nz, nx, ny >= 1");
   if (!(a_t > 0) || !(a_z > 0)) return set_error(GLASMA_ERR_INVALID_ARG, "a_t, a_z must be positive");
   if (!U || !E) return set_error(GLASMA_ERR_INVALID_ARG, "U and E are required");
+  if (((uintptr_t)U & 15) != 0) return set_error(GLASMA_ERR_INVALID_ARG, "U must be 16-byte aligned");
   if (WA < 0 || WB < 0 || (WA > 0 && (!QA || zA0 < 0 || zA0 + WA > nz)) ||
       (WB > 0 && (!QB || zB0 < 0 || zB0 + WB > nz)))
     return set_error(GLASMA_ERR_INVALID_ARG, "charge window outside the lattice or missing");

@@ -5,7 +5,8 @@
 // x fastest; x, y periodic, z open):
 //   links  complex component k of link d at site s, stored as float2 /
 //          double2:
-//          SU(2) (k = alpha, beta): U[(d*2 + k)*V + s];
+//          SU(2) (k = alpha, beta): U[(d*V + s)*2 + k], so one link is
+//          16 contiguous bytes in FP32 (one vector load) and 32 in FP64;
 //          SU(3) (k = row-major 3x3 entry), in blocks of 32 sites:
 //          U[((d*C + s/32)*9 + k)*32 + s%32] with C = ceil(V/32) blocks per
 //          direction, so the components of one link sit 32 entries apart
@@ -35,7 +36,7 @@ struct Geom {
 // and the number of complex elements of one link array (SU(3) pads V up to
 // whole blocks of 32 sites).
 GL_HD int64_t link_index(int nc, int d, int k, int64_t V, int64_t s) {
-  if (nc == 2) return (int64_t)(d * 2 + k) * V + s;
+  if (nc == 2) return ((int64_t)d * V + s) * 2 + k;
   return (((int64_t)d * ((V + 31) >> 5) + (s >> 5)) * 9 + k) * 32 + (s & 31);
 }
 GL_HD int64_t link_elems(int nc, int64_t V) { return nc == 2 ? 6 * V : 27 * 32 * ((V + 31) >> 5); }
@@ -58,8 +59,15 @@ template <typename R>
 struct LinkIO<2, R> {
   template <typename Rc>
   GL_HD static typename Group<2, Rc>::M load(const typename V2T<R>::T* U, int d, int64_t V, int64_t s) {
-    typename V2T<R>::T a = U[(int64_t)(d * 2 + 0) * V + s];
-    typename V2T<R>::T b = U[(int64_t)(d * 2 + 1) * V + s];
+    const typename V2T<R>::T* p = U + link_index(2, d, 0, V, s);
+    typename V2T<R>::T a, b;
+    if (sizeof(R) == 4) {  // alpha and beta in one 16-byte load
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      a.x = R(v.x); a.y = R(v.y); b.x = R(v.z); b.y = R(v.w);
+    } else {
+      a = p[0];
+      b = p[1];
+    }
     typename Group<2, Rc>::M m{{Rc(a.x), Rc(a.y)}, {Rc(b.x), Rc(b.y)}};
     if (DeltaConv<R, Rc>::to_full) m.a.re += Rc(1);
     return m;
@@ -70,8 +78,13 @@ struct LinkIO<2, R> {
     const Rc one = DeltaConv<R, Rc>::to_full ? Rc(1) : Rc(0);
     a.x = R(m.a.re - one); a.y = R(m.a.im);
     b.x = R(m.b.re); b.y = R(m.b.im);
-    U[(int64_t)(d * 2 + 0) * V + s] = a;
-    U[(int64_t)(d * 2 + 1) * V + s] = b;
+    typename V2T<R>::T* p = U + link_index(2, d, 0, V, s);
+    if (sizeof(R) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(float(a.x), float(a.y), float(b.x), float(b.y));
+    } else {
+      p[0] = a;
+      p[1] = b;
+    }
   }
 };
 

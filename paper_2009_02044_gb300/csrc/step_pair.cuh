@@ -56,26 +56,23 @@ template <>
 struct PairIO<2> {
   typedef LinkAlgDev2<f2> G;
   typedef G::M M;
+  // (alpha, beta) of one link are 16 contiguous bytes: one address per lane
   __device__ __forceinline__ static M load(const float2* U, int d, int64_t V, int64_t sa, int64_t sb) {
-    const float* a0 = (const float*)(U + (int64_t)(d * 2 + 0) * V);
-    const float* b0 = (const float*)(U + (int64_t)(d * 2 + 1) * V);
+    const float* pa = (const float*)(U + link_index(2, d, 0, V, sa));
+    const float* pb = (const float*)(U + link_index(2, d, 0, V, sb));
     M m;
-    m.a = cplx<f2>{f2(ldg_f32(a0 + 2 * sa), ldg_f32(a0 + 2 * sb)), f2(ldg_f32(a0 + 2 * sa + 1), ldg_f32(a0 + 2 * sb + 1))};
-    m.b = cplx<f2>{f2(ldg_f32(b0 + 2 * sa), ldg_f32(b0 + 2 * sb)), f2(ldg_f32(b0 + 2 * sa + 1), ldg_f32(b0 + 2 * sb + 1))};
+    m.a = cplx<f2>{f2(ldg_f32(pa), ldg_f32(pb)), f2(ldg_f32(pa + 1), ldg_f32(pb + 1))};
+    m.b = cplx<f2>{f2(ldg_f32(pa + 2), ldg_f32(pb + 2)), f2(ldg_f32(pa + 3), ldg_f32(pb + 3))};
     return m;
   }
   __device__ __forceinline__ static void store(float2* U, int d, int64_t V, int64_t sa, int64_t sb, const M& m,
                                                bool wa, bool wb) {
-    float2* a0 = U + (int64_t)(d * 2 + 0) * V;
-    float2* b0 = U + (int64_t)(d * 2 + 1) * V;
-    if (wa) {
-      a0[sa] = make_float2(m.a.re.v.x, m.a.im.v.x);
-      b0[sa] = make_float2(m.b.re.v.x, m.b.im.v.x);
-    }
-    if (wb) {
-      a0[sb] = make_float2(m.a.re.v.y, m.a.im.v.y);
-      b0[sb] = make_float2(m.b.re.v.y, m.b.im.v.y);
-    }
+    if (wa)
+      *reinterpret_cast<float4*>(U + link_index(2, d, 0, V, sa)) =
+          make_float4(m.a.re.v.x, m.a.im.v.x, m.b.re.v.x, m.b.im.v.x);
+    if (wb)
+      *reinterpret_cast<float4*>(U + link_index(2, d, 0, V, sb)) =
+          make_float4(m.a.re.v.y, m.a.im.v.y, m.b.re.v.y, m.b.im.v.y);
   }
 };
 

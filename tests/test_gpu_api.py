@@ -127,3 +127,32 @@ def test_device_tmunu_table_equals_host_table(G, precision):
     torch.cuda.synchronize()
     tab, H = G.glasma_tmunu(h)
     assert np.array_equal(dev.cpu().numpy(), np.asarray(tab))
+
+
+def test_allocator_without_16_byte_alignment_is_rejected(G):
+    """The state arrays are read with 16-byte vector loads, so an allocator
+    whose blocks are only 8-byte aligned is refused by glasma_init_mv,
+    which gives every block back before it returns."""
+    import ctypes as C
+    import torch
+    live = {}
+
+    @G._ALLOC_FN
+    def alloc(nbytes, stream, user):
+        base = torch.cuda.caching_allocator_alloc(int(nbytes) + 16, torch.cuda.current_device())
+        live[base + 8] = base
+        return base + 8
+
+    @G._FREE_FN
+    def free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(live.pop(ptr))
+
+    a = G.glasma_allocator()
+    a.alloc, a.free, a.user = alloc, free, None
+    p = G.make_params(gi.small_config(2))
+    out = C.c_void_p()
+    st = G.load_library().glasma_init_mv(C.byref(p), None, C.c_void_p(0), C.byref(a), C.byref(out))
+    torch.cuda.synchronize()
+    assert G.ERRORS[st] == "INVALID_ARG"
+    assert "16-byte" in G.load_library().glasma_last_error_message().decode()
+    assert not live and not out.value

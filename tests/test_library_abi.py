@@ -136,3 +136,16 @@ def test_implicit_stopping_rule_on_measured_sequences(lib):
     # FP64 units: the same sequence in FP32 units is far above FP64's floor
     assert not any(stops([1.28e6, 1.87e3, 120, 10], precision="fp64"))
     assert lib.glasma_implicit_converged(None, None, 0, 0.0, 1, None) == -1
+
+
+def test_static_residual_rejects_unaligned_links_on_the_host(lib):
+    """The links are read with 16-byte vector loads: a U address that is
+    not 16-byte aligned is refused before any GPU work (the addresses are
+    never dereferenced on the host)."""
+    from paper_2009_02044_gb300 import glasma as G
+    for nc in (2, 3):
+        with pytest.raises(G.GlasmaError) as e:
+            G.glasma_gauss_residual_static(nc, "fp32", 8, 4, 4, 1.0, 1.0,
+                                           0x10008, 0x20000)
+        assert e.value.code == "INVALID_ARG"
+        assert "16-byte" in str(e.value)

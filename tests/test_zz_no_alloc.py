@@ -32,10 +32,11 @@ def G():
 
 def _device_layout(G, h, dtype):
     """Copy a context's fields (via glasma_get_fields) into caller-owned
-    torch device tensors in the library's layout (SU(2) links and all
-    fields as structure of arrays, SU(3) links in blocks of 32 sites with
-    the nine components of a block stored one after another); the charge
-    windows cover the whole lattice."""
+    torch device tensors in the library's layout (fields as structure of
+    arrays, SU(2) links with the alpha and beta of one link adjacent,
+    SU(3) links in blocks of 32 sites with the nine components of a block
+    stored one after another); the charge windows cover the whole
+    lattice."""
     import torch
     p = h.params
     nc, na = p.nc, p.nc * p.nc - 1
@@ -45,7 +46,7 @@ def _device_layout(G, h, dtype):
     if dtype == torch.float32:      # FP32 links are stored as U - 1
         U = U - np.eye(nc)
     if nc == 2:
-        comp = np.stack([U[..., 0, 0], U[..., 0, 1]], axis=1)   # [3][2][V]
+        comp = np.stack([U[..., 0, 0], U[..., 0, 1]], axis=-1)  # [3][V][2]
     else:                                                       # [3][C][9][32]
         C = (V + 31) // 32
         pad = np.zeros((3, C * 32, 9), dtype=complex)
