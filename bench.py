@@ -74,8 +74,8 @@ def parse():
     ap.add_argument("--nz", type=int, default=0,
                     help="override the lattice length (profiling on a smaller case)")
     ap.add_argument("--kernel", default="auto",
-                    choices=["auto", "staple", "staple_pairs", "plaquette",
-                             "plaquette_256"],
+                    choices=["auto", "staple", "staple_staged", "staple_pairs",
+                             "plaquette", "plaquette_256"],
                     help="leapfrog step kernel (glasma_set_step_kernel)")
     ap.add_argument("--zlen", type=int, default=0,
                     help="z slices per block of the plaquette kernel (0 = automatic)")
@@ -108,7 +108,8 @@ def step_kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2009_02044_gb300", "csrc")
     for f in ("k_step.cu", "step_link.cuh", "link_alg.cuh", "lattice.cuh",
-              "su_n.cuh", "step_pair.cuh", "pair.cuh", "k_step_plaq.cu"):
+              "su_n.cuh", "step_pair.cuh", "pair.cuh", "k_step_plaq.cu",
+              "k_step_staged.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -120,6 +121,7 @@ def step_kernel_name(nc, precision, kernel):
     if kernel == "auto":
         kernel = "plaquette" if precision == "fp64" else "staple"
     return {"staple": "k_step_leapfrog", "staple_pairs": "k_step_pair",
+            "staple_staged": "k_step_staged",
             "plaquette": "k_step_plaq", "plaquette_256": "k_step_plaq"}[kernel]
 
 

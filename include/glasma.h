@@ -144,7 +144,10 @@ GLASMA_API int glasma_init_mv(const glasma_params* p, const double* rho_host, vo
  * terms of the semi-implicit scheme (Sec. 3, Fig. wilson (b)), iterated.
  * Enqueued on the context's stream; returns before the work completes.
  * Errors: PARTICLE_EXIT (checked on the host before any work of the
- * offending step is enqueued), NOT_CONVERGED, CUDA, INVALID_ARG.
+ * offending step is enqueued), NOT_CONVERGED, CUDA, INVALID_ARG.  A wait
+ * of the staged step kernel that ran out is reported as TIMEOUT by the
+ * next glasma_gauss_residual, glasma_tmunu, glasma_get_fields or
+ * glasma_get_state.
  */
 GLASMA_API int glasma_step(glasma_ctx* c, int n_steps);
 
@@ -368,6 +371,18 @@ GLASMA_API int glasma_slab_unpack(glasma_ctx* c, int dir, const void* dev_buf);
  *                              (x, y, z) and (x, y, z + ceil(nz/2)), in the
  *                              two lanes of the packed FP32 instructions
  *                              (FP32 state only);
+ *   GLASMA_KERNEL_STAPLE_STAGED the staple kernel with the links of two
+ *                              transverse rows (plus a one-row halo) of four
+ *                              consecutive z slices held in shared memory,
+ *                              the next slice copied in by the bulk-copy
+ *                              engine while the current one is updated; a
+ *                              block marches through a chunk of slices.
+ *                              Bitwise the staple kernel's result.  FP32
+ *                              SU(3) state of a whole lattice (not a slab)
+ *                              with nx = 32 or 64 only.  A wait on a copy
+ *                              that runs out (glasma_set_staging_wait) is
+ *                              reported as TIMEOUT by the next call that
+ *                              returns host values;
  *   GLASMA_KERNEL_AUTO         the default, from GB300 timings: for FP64
  *                              state the plaquette kernel where a transverse
  *                              row fits one block (nx <= 320; its 24% fewer
@@ -375,7 +390,7 @@ GLASMA_API int glasma_slab_unpack(glasma_ctx* c, int dir, const void* dev_buf);
  *                              step), else the staple kernel; for FP32 the
  *                              staple kernel. */
 enum { GLASMA_KERNEL_AUTO = 0, GLASMA_KERNEL_STAPLE = 1, GLASMA_KERNEL_PLAQUETTE = 2,
-       GLASMA_KERNEL_PLAQUETTE_256 = 3, GLASMA_KERNEL_STAPLE_PAIRS = 4 };
+       GLASMA_KERNEL_PLAQUETTE_256 = 3, GLASMA_KERNEL_STAPLE_PAIRS = 4, GLASMA_KERNEL_STAPLE_STAGED = 5 };
 
 /*
  * Choose the leapfrog step kernel of a context and, for the plaquette
@@ -385,9 +400,22 @@ enum { GLASMA_KERNEL_AUTO = 0, GLASMA_KERNEL_STAPLE = 1, GLASMA_KERNEL_PLAQUETTE
  * choice never changes the state's layout, so it may change between steps.
  * Errors: INVALID_ARG (unknown kernel, zlen outside [0, nz], a plaquette
  * kernel asked for on a lattice whose transverse rows do not fit one
- * block, the paired kernel asked for on FP64 state).
+ * block, the paired kernel asked for on FP64 state, the staged kernel
+ * asked for outside FP32 SU(3) whole lattices with nx = 32 or 64).
  */
 GLASMA_API int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen);
+
+/*
+ * Spin budget of one wait of the staged step kernel on its shared-memory
+ * copies, in SM clock cycles (default 2^31, about a second; at most 2^40),
+ * and stall (0 or 1, default 0).  stall = 1 makes the first block of every
+ * staged launch also wait on a barrier that nothing completes, so that its
+ * wait runs out and the launch reports TIMEOUT: it exists to test the
+ * timeout path and has no other use.  After a wait runs out the block stops,
+ * waits for its copies in flight and records the failure; the state after
+ * that step is undefined.  Errors: INVALID_ARG.
+ */
+GLASMA_API int glasma_set_staging_wait(glasma_ctx* c, long long wait_cycles, int stall);
 
 /*
  * Rest-frame analysis of sampled tables (Sec. 4: the event average of

@@ -131,9 +131,10 @@ static int check_params(const glasma_params* p) {
 // The automatic choice, from CUDA-event timings on GB300: in FP64 the
 // plaquette kernel (24% fewer FMAs, and the FP64 pipe bounds the step:
 // 12.8 against 15.3 ms per SU(3) 512 x 64^2 step); in FP32 SU(3) the
-// one-site staple kernel (0.469 ms, against 0.521 for the plaquette kernel
-// and 0.572 for site pairs, whose 168 registers leave too few warps to hide
-// latency); in FP32 SU(2) the staple kernel too (1.10 against 1.39 ms for
+// one-site staple kernel (0.469 ms, against 0.521 for the plaquette kernel,
+// 0.572 for site pairs, whose 168 registers leave too few warps to hide
+// latency, and 0.47-0.49 for the staged staple kernel, bitwise the same
+// result); in FP32 SU(2) the staple kernel too (1.10 against 1.39 ms for
 // site pairs per 1024 x 128^2 step, once a link's alpha and beta became one
 // 16-byte load: the pairs' 32-bit loads then stride 16 bytes).
 bool use_plaq_kernel(const glasma_ctx* c) {
@@ -146,9 +147,14 @@ bool use_pair_kernel(const glasma_ctx* c) {
   return c->step_kernel == GLASMA_KERNEL_STAPLE_PAIRS;
 }
 
+bool use_staged_kernel(const glasma_ctx* c) {
+  return c->step_kernel == GLASMA_KERNEL_STAPLE_STAGED && staged_fits(c);
+}
+
 int launch_step_chosen(glasma_ctx* c, bool hop) {
   if (use_plaq_kernel(c)) return launch_step_plaq(c, hop, c->step_zlen);
   if (use_pair_kernel(c)) return launch_step_pair(c, hop);
+  if (use_staged_kernel(c)) return launch_step_staged(c, hop);
   return launch_step_leapfrog(c, hop);
 }
 
@@ -416,7 +422,8 @@ int glasma_gauss_residual(glasma_ctx* c, double* max_abs, double* rms, double* r
   if (max_abs) *max_abs = r[0];
   if (rms) *rms = r[1];
   if (rho_max) *rho_max = r[2];
-  return st;
+  const int ss = staged_status(c);
+  return ss ? ss : st;
 }
 
 int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total) {
@@ -437,6 +444,8 @@ int glasma_tmunu(glasma_ctx* c, double* out, double* energy_total) {
   }
   if (out) memcpy(out, tab.data() + 4 * (size_t)c->lo, sizeof(double) * 4 * (size_t)(c->hi - c->lo));
   if (energy_total) *energy_total = c->p.a_t * c->p.a_t * c->p.a_z * (double)c->g.nxy * sum;
+  st = staged_status(c);
+  if (st) return st;
   if (bad) return set_error(GLASMA_ERR_NONFINITE, "T^{mu nu} met a non-finite value");
   return GLASMA_OK;
 }
@@ -598,7 +607,7 @@ int glasma_get_fields(glasma_ctx* c, double* U, double* E, double* QA, double* Q
       }
   }
   if (step_n) *step_n = c->n;
-  return GLASMA_OK;
+  return staged_status(c);
 }
 
 static int upload_links(glasma_ctx* c, void* dev, const double* U) {
@@ -795,7 +804,7 @@ int glasma_get_state(glasma_ctx* c, void* host_buf, size_t bytes) {
     memcpy(out + off + sizes[k], &crc, sizeof(crc));
     off += sizes[k] + sizeof(crc);
   }
-  return GLASMA_OK;
+  return staged_status(c);
 }
 
 int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes) {
@@ -873,10 +882,14 @@ int glasma_set_state(glasma_ctx* c, const void* host_buf, size_t bytes) {
 int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen) {
   if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
   if (kernel != GLASMA_KERNEL_AUTO && kernel != GLASMA_KERNEL_STAPLE && kernel != GLASMA_KERNEL_PLAQUETTE &&
-      kernel != GLASMA_KERNEL_PLAQUETTE_256 && kernel != GLASMA_KERNEL_STAPLE_PAIRS)
+      kernel != GLASMA_KERNEL_PLAQUETTE_256 && kernel != GLASMA_KERNEL_STAPLE_PAIRS &&
+      kernel != GLASMA_KERNEL_STAPLE_STAGED)
     return set_error(GLASMA_ERR_INVALID_ARG, "unknown step kernel");
   if (kernel == GLASMA_KERNEL_STAPLE_PAIRS && (c->rs != 4 || c->slab))
     return set_error(GLASMA_ERR_INVALID_ARG, "the paired staple kernel needs FP32 state of a whole lattice");
+  if (kernel == GLASMA_KERNEL_STAPLE_STAGED && !staged_fits(c))
+    return set_error(GLASMA_ERR_INVALID_ARG,
+                     "the staged staple kernel needs FP32 SU(3) state of a whole lattice with nx = 32 or 64");
   if (zlen < 0 || zlen > c->g.nz) return set_error(GLASMA_ERR_INVALID_ARG, "zlen must be in [0, nz]");
   const int old = c->step_kernel;
   c->step_kernel = kernel;
@@ -885,6 +898,15 @@ int glasma_set_step_kernel(glasma_ctx* c, int kernel, int zlen) {
     return set_error(GLASMA_ERR_INVALID_ARG, "transverse rows too long for the plaquette kernel");
   }
   c->step_zlen = zlen;
+  return GLASMA_OK;
+}
+
+int glasma_set_staging_wait(glasma_ctx* c, long long wait_cycles, int stall) {
+  if (!c) return set_error(GLASMA_ERR_INVALID_ARG, "context is NULL");
+  if (wait_cycles < 1 || wait_cycles > (1ll << 40) || (stall != 0 && stall != 1))
+    return set_error(GLASMA_ERR_INVALID_ARG, "wait_cycles must be in [1, 2^40] and stall 0 or 1");
+  c->staged_wait = wait_cycles;
+  c->staged_stall = stall;
   return GLASMA_OK;
 }
 

@@ -43,6 +43,12 @@ struct glasma_ctx {
   int step_kernel = 0;        // GLASMA_KERNEL_* of the leapfrog step
   int step_zlen = 0;          // z slices per block of the plaquette kernel (0 = automatic)
   bool plaq_ready = false;    // the plaquette kernel's attributes are set on this device
+  // staged step kernel (k_step_staged.cu): spin budget of one wait on its
+  // copies (SM cycles), the timeout test's stall, and whether it has run
+  // since its status word (dflag[1]) was last read
+  long long staged_wait = 1ll << 31;
+  int staged_stall = 0;
+  bool staged_launched = false;
   // z slab of a lattice split along the beam axis (glasma_slab_init): the
   // context's lattice is the slab with its halo slices; local slice 0 is
   // global slice zoff; the owned slices are [lo, hi), the others halos.  An
@@ -89,9 +95,16 @@ int launch_step_leapfrog(glasma_ctx* c, bool hop);
 int launch_step_plaq(glasma_ctx* c, bool hop, int zlen);
 bool plaq_fits(const glasma_ctx* c);
 // the step kernel glasma_step launches for this context: plaquette, staple
-// on site pairs (FP32) or staple
+// on site pairs (FP32), staged staple (FP32 SU(3)) or staple
 bool use_plaq_kernel(const glasma_ctx* c);
 bool use_pair_kernel(const glasma_ctx* c);
+bool use_staged_kernel(const glasma_ctx* c);
+// staple kernel with the links staged in shared memory by bulk copies
+// (FP32 SU(3), rows of 32 or 64 sites, whole lattices)
+bool staged_fits(const glasma_ctx* c);
+int launch_step_staged(glasma_ctx* c, bool hop);
+// TIMEOUT if a staged launch recorded a wait that ran out (synchronises)
+int staged_status(glasma_ctx* c);
 int launch_step_chosen(glasma_ctx* c, bool hop);
 // staple kernel on pairs of sites (t, iz), (t, iz + ceil(nz/2)), FP32 only
 int launch_step_pair(glasma_ctx* c, bool hop);

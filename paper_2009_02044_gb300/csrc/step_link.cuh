@@ -31,18 +31,19 @@ struct StepArgs {
 //       with Gauss weights 1/a_i^2);
 //   (2) E += dt F (+ dt J on the z link);
 //   (3) write exp(i dt E) U to the other link buffer (re-unitarised in FP32).
-// Shared by the staple kernel below and the plaquette kernel
-// (k_step_plaq.cu), so both apply the same update arithmetic.
+// Shared by the staple kernel below, the plaquette kernel (k_step_plaq.cu)
+// and the staged kernel (k_step_staged.cu), so all apply the same update
+// arithmetic.  update_link_ue takes the link U_i(x) and the field
+// E_i(t_{n-1/2}) already loaded (Ui, E0); update_link loads them.
 template <int NC, typename R>
-__device__ __forceinline__ void update_link(const StepArgs<R>& a, int i, uint32_t t, int iz, int64_t s,
-                                            const R* F) {
+__device__ __forceinline__ void update_link_ue(const StepArgs<R>& a, int i, uint32_t t, int iz, int64_t s,
+                                               const R* F, const typename LinkAlg<NC, R>::M& Ui, const R* E0) {
   typedef LinkAlg<NC, R> G;
   typedef typename G::M M;
   constexpr int NA = G::NA;
-  const M Ui = LinkIO<NC, R>::template load<R>(a.U, i, a.g.V, s);
   R e[NA];
 #pragma unroll
-  for (int c = 0; c < NA; ++c) e[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s] + a.dt * F[c];
+  for (int c = 0; c < NA; ++c) e[c] = E0[c] + a.dt * F[c];
   if (i == 2 && a.hop) {
     R dj[NA];
 #pragma unroll
@@ -78,6 +79,17 @@ __device__ __forceinline__ void update_link(const StepArgs<R>& a, int i, uint32_
   M un = G::mul(G::expi(e, a.dt), Ui);
   if (sizeof(R) == 4) un = G::reunit(un);
   LinkIO<NC, R>::template store<R>(a.Un, i, a.g.V, s, un);
+}
+
+template <int NC, typename R>
+__device__ __forceinline__ void update_link(const StepArgs<R>& a, int i, uint32_t t, int iz, int64_t s,
+                                            const R* F) {
+  constexpr int NA = LinkAlg<NC, R>::NA;
+  const typename LinkAlg<NC, R>::M Ui = LinkIO<NC, R>::template load<R>(a.U, i, a.g.V, s);
+  R E0[NA];
+#pragma unroll
+  for (int c = 0; c < NA; ++c) E0[c] = a.E[(int64_t)(i * NA + c) * a.g.V + s];
+  update_link_ue<NC, R>(a, i, t, iz, s, F, Ui, E0);
 }
 
 // Link i of the site with transverse index t on slice iz, its force from

@@ -25,7 +25,7 @@ ERRORS = {
 FP64, FP32 = 0, 1
 LEAPFROG, IMPLICIT = 0, 1
 KERNELS = {"auto": 0, "staple": 1, "plaquette": 2, "plaquette_256": 3,
-           "staple_pairs": 4}
+           "staple_pairs": 4, "staple_staged": 5}
 
 
 class GlasmaError(RuntimeError):
@@ -95,6 +95,7 @@ def load_library(path=LIB_PATH):
         "glasma_set_state": (C.c_int, [P, P, C.c_size_t]),
         "glasma_get_info": (C.c_int, [P, C.POINTER(glasma_info)]),
         "glasma_set_step_kernel": (C.c_int, [P, C.c_int, C.c_int]),
+        "glasma_set_staging_wait": (C.c_int, [P, C.c_longlong, C.c_int]),
         "glasma_slab_init": (C.c_int, [C.POINTER(glasma_params), dp, C.c_int,
                                        C.c_int, P, C.POINTER(glasma_allocator),
                                        C.POINTER(C.c_void_p)]),
@@ -385,11 +386,20 @@ def glasma_get_info(h):
 
 def glasma_set_step_kernel(h, kernel="auto", zlen=0):
     """Leapfrog step kernel of the context: "auto", "staple", "plaquette",
-    "plaquette_256" or "staple_pairs" (FP32); zlen = z slices per block of
-    the plaquette kernel (0 = automatic)."""
+    "plaquette_256", "staple_pairs" (FP32) or "staple_staged" (FP32 SU(3),
+    nx = 32 or 64); zlen = z slices per block of the plaquette kernel
+    (0 = automatic)."""
     _check(load_library().glasma_set_step_kernel(h.ptr, KERNELS[kernel],
                                                  int(zlen)),
            "glasma_set_step_kernel")
+
+
+def glasma_set_staging_wait(h, wait_cycles=1 << 31, stall=False):
+    """Spin budget (SM cycles) of one wait of the staged step kernel, and
+    the stall that makes a wait run out (for testing the timeout path)."""
+    _check(load_library().glasma_set_staging_wait(h.ptr, int(wait_cycles),
+                                                  1 if stall else 0),
+           "glasma_set_staging_wait")
 
 
 def glasma_slab_set_windows(h, window_a, window_b):

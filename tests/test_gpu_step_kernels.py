@@ -1,5 +1,6 @@
-"""The two leapfrog step kernels (staple form and plaquette-centric form,
-glasma_set_step_kernel) against the FP64 oracle, through the C ABI.
+"""The leapfrog step kernels (staple form, plaquette-centric form, site
+pairs and the staged staple form, glasma_set_step_kernel) against the FP64
+oracle and one another, through the C ABI.
 
 The plaquette kernel splits the lattice into blocks of whole transverse rows
 with a -y halo row, marching through z in chunks with a warm-up slice; the
@@ -270,3 +271,90 @@ def test_longest_lattice_matches_oracle(G, nc):
     U, E, QA, QB, n = G.glasma_get_fields(h)
     assert rel(U, ref.U) < 1.5e-6 and rel(E, ref.E) < 1.5e-6
     G.glasma_free(h)
+
+
+# The staged staple kernel (links of two rows and their halo rows, four z
+# slices, in shared memory): rows of 64 sites (two link blocks per row) and
+# of 32 (one); a chunk of one slice (nz below the chunk count); a ragged last
+# tile (odd ny); fewer rows than the staged image holds, so rows repeat
+# (ny = 3, ny = 1).
+STAGED_SHAPES = [(8, 64, 64), (23, 7, 64), (40, 64, 64), (30, 3, 32), (5, 1, 64)]
+
+
+@pytest.mark.parametrize("shape", STAGED_SHAPES)
+def test_staged_kernel_is_bitwise_the_staple_kernel(G, shape):
+    """The staged kernel performs the staple kernel's arithmetic in the same
+    order from shared-memory copies of the same links: after 5 steps (hops
+    at 0, 2 and 4, charges of both nuclei) every link, field and charge is
+    bitwise the staple kernel's, and within the FP32 bound of the oracle."""
+    nz, ny, nx = shape
+    st = _random_state(3, nz, ny, nx, seed=31 * nz + ny)
+    out = []
+    for kernel in ("staple", "staple_staged"):
+        h = _ctx(G, st, "fp32")
+        G.glasma_set_step_kernel(h, kernel)
+        G.glasma_step(h, 5)
+        out.append(G.glasma_get_fields(h))
+        G.glasma_free(h)
+    for x, y in zip(out[0][:4], out[1][:4]):
+        assert np.array_equal(x, y)
+    assert out[0][4] == out[1][4] == 5
+    ref = O.step(st, 5)
+    U, E, QA, QB, n = out[1]
+    errs = dict(U=rel(U, ref.U), E=rel(E, ref.E), QA=rel(QA, ref.QA), QB=rel(QB, ref.QB))
+    assert all(v < 2.5e-6 for v in errs.values()), errs
+
+
+def test_staged_kernel_through_a_collision(G):
+    """Through a collision on 64-site rows: the staged kernel and the
+    automatic choice give bitwise the staple kernel's state and table."""
+    cfg = dict(gi.small_config(3, nz=48, nx=64, ny=6, sigma_l=2.0), precision="fp32")
+    rho = gi.mv_rho(cfg["seed"], 3, cfg["nx"], cfg["ny"], cfg["g2mu"])
+    res = []
+    for kernel in ("staple", "staple_staged", "auto"):
+        h = G.glasma_init_mv(cfg, rho)
+        G.glasma_set_step_kernel(h, kernel)
+        G.glasma_step(h, 40)
+        res.append((G.glasma_get_fields(h)[:4], G.glasma_tmunu(h)[0]))
+        G.glasma_free(h)
+    for other in res[1:]:
+        for x, y in zip(res[0][0], other[0]):
+            assert np.array_equal(x, y)
+        assert np.array_equal(res[0][1], other[1])
+
+
+def test_staged_wait_that_runs_out_is_reported(G):
+    """A wait of the staged kernel on a barrier that nothing completes (the
+    stall switch) runs out after its budget; the block stops, waits for its
+    copies in flight, and the next call that returns host values reports
+    TIMEOUT once.  No GPU fault: the wait is bounded and the copies land."""
+    st = _random_state(3, 8, 64, 64, seed=4)
+    h = _ctx(G, st, "fp32")
+    G.glasma_set_step_kernel(h, "staple_staged")
+    G.glasma_set_staging_wait(h, 1 << 20, stall=True)
+    G.glasma_step(h, 1)
+    with pytest.raises(G.GlasmaError) as e:
+        G.glasma_tmunu(h)
+    assert e.value.code == "TIMEOUT"
+    G.glasma_set_staging_wait(h, 1 << 31, stall=False)
+    G.glasma_step(h, 1)
+    tab, H = G.glasma_tmunu(h)   # reported once; the status word is clear again
+    assert np.all(np.isfinite(tab))
+    G.glasma_free(h)
+
+
+def test_staged_kernel_rejects_what_it_does_not_stage(G):
+    cases = [dict(gi.small_config(3, nx=40), precision="fp32"),      # nx not 32 or 64
+             dict(gi.small_config(2, nx=64), precision="fp32"),      # SU(2)
+             dict(gi.small_config(3, nx=64), precision="fp64")]      # FP64
+    for cfg in cases:
+        h = G.glasma_init_mv(cfg, None)
+        with pytest.raises(G.GlasmaError) as e:
+            G.glasma_set_step_kernel(h, "staple_staged")
+        assert e.value.code == "INVALID_ARG"
+        for wait, stall in ((0, 0), (1 << 41, 0), (1 << 20, 2)):
+            with pytest.raises(G.GlasmaError) as e:
+                G._check(G.load_library().glasma_set_staging_wait(h.ptr, wait, stall),
+                         "glasma_set_staging_wait")
+            assert e.value.code == "INVALID_ARG"
+        G.glasma_free(h)
