@@ -132,7 +132,7 @@ def test_fp32_kernels_match_oracle(G, nc, shape, kernel):
 
 @pytest.mark.parametrize("nc", [2, 3])
 def test_paired_kernel_through_a_collision_fp32(G, nc):
-    """The paired staple kernel (the FP32 default) on the ragged 47 x 10 x 12
+    """The paired staple kernel on the ragged 47 x 10 x 12
     collision (odd nz) through the crossing, against the FP64 oracle at the
     FP32 bound of the other collision tests, and against the one-site staple
     kernel at the rounding level of 40 steps."""
