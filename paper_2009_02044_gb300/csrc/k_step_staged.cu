@@ -6,22 +6,30 @@
 // A block owns kStR full transverse rows (x is periodic inside a row) and
 // marches through a chunk of z slices.  The links of the rows iy0 - 1 ..
 // iy0 + kStR (a one-row halo on each side) of four consecutive slices live
-// in shared memory: the update of slice z reads slices z - 1, z and z + 1
-// while slice z + 2 is copied in by cp.async.bulk (one copy per row and
-// direction; the copies of a slice complete one phase of that slot's
-// mbarrier).  A row of one direction is the contiguous run of its 32-site
+// in shared memory (four slots): the update of slice z reads slices z - 1,
+// z and z + 1.  A row of one direction is the contiguous run of its 32-site
 // link blocks (the SU(3) layout of lattice.cuh), so the shared image keeps
 // the global block layout and a warp reads 32 consecutive sites of one
-// component.  One thread per link, all three directions of the tile's sites
-// in one block; every link update performs exactly the arithmetic of
-// step_link, in the same order, so the result is bitwise that of the
-// staple kernel.
+// component.  One consumer thread per link, all three directions of the
+// tile's sites in one block; every link update performs exactly the
+// arithmetic of step_link, in the same order, so the result is bitwise that
+// of the staple kernel.
 //
-// Every wait on a copy is bounded (staged_wait SM cycles, about a second by
-// default).  A wait that runs out makes the whole block stop after the
-// slice it is on, wait (bounded) for its copies still in flight, and set
-// the context's staged status word, which the next call that returns host
-// values reports as GLASMA_ERR_TIMEOUT.
+// One more warp produces: its first lane copies slice s into slot s % 4
+// with cp.async.bulk (one copy per row and direction, the bytes counted on
+// the slot's full barrier) as soon as every consumer thread has released
+// slice s - 4 on the slot's empty barrier.  A consumer releases slice z - 1
+// after its update of slice z, the last one that reads it.  No barrier
+// spans the block after the start, so warps run up to a slice apart and the
+// copies run up to three slices ahead.
+//
+// Every wait is bounded (staged_wait SM cycles, about a second by default).
+// A consumer whose wait runs out stops and raises the block's abort flag;
+// the other consumers stop at their next slice; the producer stops issuing,
+// waits (bounded) for the copies it has in flight, and, being the last
+// thread to use the block's shared memory, exits after them.  The context's
+// staged status word is set, and the next call that returns host values
+// reports GLASMA_ERR_TIMEOUT.
 #include "step_link.cuh"
 
 namespace glasma {
@@ -68,8 +76,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
   return true;
 }
 
-// The drain after a failed wait always allows 2^31 cycles: copies in flight
-// must land before the block's shared memory is released.
+// The producer's wait for its copies in flight always allows 2^31 cycles:
+// they must land before the block's shared memory is released.
 constexpr long long kStDrainCycles = 1ll << 31;
 
 template <int RB>
@@ -78,13 +86,14 @@ struct StagedGeo {
   static constexpr int ROWS = kStR + 2;
   static constexpr int DIRB = ROWS * RB * 288;  // float2 per (slot, direction)
   static constexpr int SLOTB = 3 * DIRB;        // float2 per slot
-  static constexpr int THREADS = 3 * kStR * NX;
-  // the slots, then kStSlots + 1 barriers (the last one is armed by nothing:
-  // the stall test waits on it)
-  static constexpr size_t smem = (size_t)kStSlots * SLOTB * sizeof(float2) + (kStSlots + 1) * sizeof(unsigned long long);
+  static constexpr int CONSUMERS = 3 * kStR * NX;
+  static constexpr int THREADS = CONSUMERS + 32;  // one producer warp
+  // the slots, then a full and an empty barrier per slot and one barrier
+  // that nothing completes (the stall test waits on it)
+  static constexpr size_t smem =
+      (size_t)kStSlots * SLOTB * sizeof(float2) + (2 * kStSlots + 1) * sizeof(unsigned long long);
 };
 
-// Link d at shared row rr, column ix of the slice held in slot q.
 template <int RB>
 __device__ __forceinline__ LinkAlg<3, float>::M st_load(const float2* sm, int q, int d, int rr, int ix) {
   typedef StagedGeo<RB> SG;
@@ -98,15 +107,23 @@ __device__ __forceinline__ LinkAlg<3, float>::M st_load(const float2* sm, int q,
   return m;
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(b)) : "memory");
+}
+
 struct StagedArgs {
   StepArgs<float> s;
-  int zhi;             // one past the last slice updated (s.zlo is the first)
-  int zlen;            // slices per block
-  long long wait;      // SM cycles one wait on a copy may take
-  int stall;           // 1: block (0, 0) also waits on the unarmed barrier
-  int* status;         // set to 1 when a wait ran out
+  int zhi;
+  int zlen;
+  long long wait;
+  int stall;
+  int* status;
 };
 
+// Producer warp (lane 0): slice zs goes to slot zs & 3 once the slice four
+// before it has been released by every consumer thread (empty barrier).
+// Consumers: wait for the slice's full barrier, update, release slice z - 1
+// after iteration z (its last reader).
 template <int RB>
 __global__ void __launch_bounds__(StagedGeo<RB>::THREADS, 1) k_step_staged(StagedArgs sa) {
   typedef StagedGeo<RB> SG;
@@ -115,125 +132,140 @@ __global__ void __launch_bounds__(StagedGeo<RB>::THREADS, 1) k_step_staged(Stage
   constexpr int NX = SG::NX, ROWS = SG::ROWS;
   extern __shared__ __align__(128) unsigned char st_raw[];
   float2* sm = (float2*)st_raw;
-  unsigned long long* bar = (unsigned long long*)(st_raw + (size_t)kStSlots * SG::SLOTB * sizeof(float2));
+  unsigned long long* full = (unsigned long long*)(st_raw + (size_t)kStSlots * SG::SLOTB * sizeof(float2));
+  unsigned long long* empty = full + kStSlots;
+  unsigned long long* unarmed = full + 2 * kStSlots;
+  __shared__ volatile int abort_flag;
   const StepArgs<float>& a = sa.s;
   const Geom& g = a.g;
   const int tid = threadIdx.x;
-  const int i = tid / (kStR * NX);  // link direction of this thread
-  const int loc = tid - i * (kStR * NX);
-  const int r = loc / NX, ix = loc - r * NX;  // interior row and column
   const int iy0 = blockIdx.x * kStR;
-  const int iy = iy0 + r;
-  const bool inner = iy < g.ny;  // the last tile of an odd ny has one row
-  const uint32_t t = (uint32_t)(inner ? iy : 0) * NX + ix;
   const int z0 = a.zlo + blockIdx.y * sa.zlen;
   const int z1 = min(z0 + sa.zlen, sa.zhi);
-  // slices the chunk reads: z0 - 1 .. z1 inside the lattice
   const int lo_load = max(z0 - 1, 0), hi_load = min(z1, g.nz - 1);
-  const int64_t C = (g.V + 31) >> 5;  // link blocks per direction
-  const int64_t bps = g.nxy >> 5;     // link blocks per slice
-  const unsigned slice_bytes = 3u * ROWS * RB * 2304u;
-
-  auto load_slice = [&](int zs) {
-    const int q = zs & (kStSlots - 1);
-    mbar_expect_tx(&bar[q], slice_bytes);
-    for (int d = 0; d < 3; ++d)
-      for (int rr = 0; rr < ROWS; ++rr) {
-        const int gy = ((iy0 - 1 + rr) % g.ny + g.ny) % g.ny;  // periodic y; rows repeat when ny < ROWS
-        const float2* src = a.U + (((int64_t)d * C + (int64_t)zs * bps + (int64_t)gy * RB) * 9) * 32;
-        bulk_to_smem(sm + (q * 3 + d) * SG::DIRB + rr * RB * 288, src, RB * 2304u, &bar[q]);
-      }
-  };
-
   if (tid == 0) {
-    for (int q = 0; q <= kStSlots; ++q) mbar_init(&bar[q], 1);
+    abort_flag = 0;
+    for (int q = 0; q < kStSlots; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], SG::CONSUMERS);
+    }
+    mbar_init(unarmed, 1);
     mbar_fence_init();
   }
   __syncthreads();
-  unsigned pending = 0;  // bit q: a copy into slot q not waited for yet (thread 0's record)
-  if (tid == 0)
-    for (int zs = lo_load; zs <= min(z0 + 1, hi_load); ++zs) {
-      load_slice(zs);
-      pending |= 1u << (zs & (kStSlots - 1));
-    }
-  unsigned phase = 0;  // bit q: parity of the next completion of slot q
-  int failed = 0;      // a wait of this thread ran out
-  auto wait_slice = [&](int zs) {
-    const int q = zs & (kStSlots - 1);
-    if (mbar_wait(&bar[q], (phase >> q) & 1u, sa.wait)) {
-      phase ^= 1u << q;
-      pending &= ~(1u << q);
-    } else {
-      failed = 1;
-    }
-  };
-  if (sa.stall && blockIdx.x == 0 && blockIdx.y == 0 && !mbar_wait(&bar[kStSlots], 0, sa.wait)) failed = 1;
-  for (int zs = lo_load; zs <= min(z0, hi_load); ++zs) wait_slice(zs);
-  for (int z = z0; z < z1; ++z) {
-    // every thread has left slice z - 1, so the slot of slice z - 2 may be
-    // refilled; the block leaves together if any wait ran out
-    if (__syncthreads_or(failed)) break;
-    if (tid == 0 && z + 2 <= hi_load) {
-      fence_proxy_async();
-      load_slice(z + 2);
-      pending |= 1u << ((z + 2) & (kStSlots - 1));
-    }
-    if (z + 1 <= hi_load) wait_slice(z + 1);
-    if (!inner || (i == 2 && z == g.nz - 1)) continue;  // no z link on the last slice
-    const int q0 = z & 3, qm = (z - 1) & 3, qp = (z + 1) & 3;
-    const int rr0 = r + 1;
-    const int xp = ix + 1 == NX ? 0 : ix + 1, xm = ix == 0 ? NX - 1 : ix - 1;
-    const int64_t s = (int64_t)z * g.nxy + t;
-    float E0[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) E0[c] = a.E[(int64_t)(i * 8 + c) * g.V + s];
-    // shared coordinates (slot, row, column) of x + e_d (sgn = 1) or x - e_d
-    auto nb = [&](int d, int sgn, int& q, int& rr, int& cx) {
-      q = q0;
-      rr = rr0;
-      cx = ix;
-      if (d == 0) cx = sgn > 0 ? xp : xm;
-      else if (d == 1) rr = rr0 + sgn;
-      else q = sgn > 0 ? qp : qm;
-    };
-    // the staple sum of link_force_staple, term by term in its order
-    G::Sum S = G::zero_sum();
-    const float wt = a.w[0], wz = a.w[2];
-#pragma unroll 1
-    for (int j = 0; j < 3; ++j) {
-      if (j == i) continue;
-      const float wj = j == 2 ? wz : wt;
-      const bool fwd = (j != 2) || (z <= g.nz - 2);
-      const bool bwd = (j != 2) || (z >= 1);
-      int qi, ri, ci, qj, rj, cj_, qn, rn, cn;
-      nb(i, +1, qi, ri, ci);   // x + e_i
-      nb(j, +1, qj, rj, cj_);  // x + e_j
-      nb(j, -1, qn, rn, cn);   // x - e_j
-      if (fwd) {
-        M T = G::mul_d(st_load<RB>(sm, qi, j, ri, ci), st_load<RB>(sm, qj, i, rj, cj_));
-        T = G::mul_d(T, st_load<RB>(sm, q0, j, rr0, ix));
-        G::sum_add(S, wj, T);
+  if (tid >= SG::CONSUMERS) {
+    // ---- producer ----
+    if (tid != SG::CONSUMERS) return;
+    const int64_t C = (g.V + 31) >> 5;
+    const int64_t bps = g.nxy >> 5;
+    const unsigned slice_bytes = 3u * ROWS * RB * 2304u;
+    int issued = lo_load - 1;
+    bool ok = !(sa.stall && blockIdx.x == 0 && blockIdx.y == 0 && !mbar_wait(unarmed, 0, sa.wait));
+    for (int zs = lo_load; zs <= hi_load && ok; ++zs) {
+      const int q = zs & (kStSlots - 1);
+      const int k = (zs - lo_load) >> 2;  // use of this slot
+      if (k > 0) {
+        // the slice four before has been released (bounded, and given up
+        // if a consumer has aborted)
+        const long long t0 = clock64();
+        while (!mbar_test(&empty[q], (unsigned)((k - 1) & 1))) {
+          if (abort_flag || clock64() - t0 > sa.wait) {
+            ok = false;
+            break;
+          }
+        }
+        if (!ok) break;
+        fence_proxy_async();
       }
-      if (bwd) {
-        // x + e_i - e_j: the offsets of the two directions add
-        const int qd = i == 2 ? qp : qn, rd = rn + ri - rr0, cd = i == 0 ? ci : cn;
-        M T = G::mul(st_load<RB>(sm, qn, i, rn, cn), st_load<RB>(sm, qd, j, rd, cd));
-        T = G::d_mul(T, st_load<RB>(sm, qn, j, rn, cn));
-        G::sum_add(S, wj, T);
-      }
+      mbar_expect_tx(&full[q], slice_bytes);
+      for (int d = 0; d < 3; ++d)
+        for (int rr = 0; rr < ROWS; ++rr) {
+          const int gy = ((iy0 - 1 + rr) % g.ny + g.ny) % g.ny;
+          const float2* src = a.U + (((int64_t)d * C + (int64_t)zs * bps + (int64_t)gy * RB) * 9) * 32;
+          bulk_to_smem(sm + (q * 3 + d) * SG::DIRB + rr * RB * 288, src, RB * 2304u, &full[q]);
+        }
+      issued = zs;
     }
-    float pr[8], F[8];
-    const M Ui = st_load<RB>(sm, q0, i, rr0, ix);
-    G::proj_mul_sum(Ui, S, pr);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) F[c] = -pr[c];
-    update_link_ue<3, float>(a, i, t, z, s, F, Ui, E0);
+    // the copies still in flight land before this thread (the last user of
+    // the block's shared memory) may exit
+    for (int zs = max(lo_load, issued - 3); zs <= issued; ++zs)
+      mbar_wait(&full[zs & (kStSlots - 1)], (unsigned)(((zs - lo_load) >> 2) & 1), kStDrainCycles);
+    if (!ok) {
+      abort_flag = 1;
+      atomicExch(sa.status, 1);
+    }
+    return;
   }
-  if (__syncthreads_or(failed) && tid == 0) {
-    // a wait ran out: wait for the copies still in flight before the
-    // block's shared memory is released, and record the failure
-    for (int q = 0; q < kStSlots; ++q)
-      if (pending & (1u << q)) mbar_wait(&bar[q], (phase >> q) & 1u, kStDrainCycles);
+  // ---- consumers ----
+  const int i = tid / (kStR * NX);
+  const int loc = tid - i * (kStR * NX);
+  const int r = loc / NX, ix = loc - r * NX;
+  const int iy = iy0 + r;
+  const bool inner = iy < g.ny;
+  const uint32_t t = (uint32_t)(inner ? iy : 0) * NX + ix;
+  auto wait_full = [&](int zs) -> bool {
+    return mbar_wait(&full[zs & (kStSlots - 1)], (unsigned)(((zs - lo_load) >> 2) & 1), sa.wait);
+  };
+  bool good = true;
+  for (int zs = lo_load; zs <= min(z0, hi_load) && good; ++zs) good = wait_full(zs);
+  for (int z = z0; z < z1 && good; ++z) {
+    if (abort_flag) break;
+    if (z + 1 <= hi_load && !wait_full(z + 1)) {
+      good = false;
+      break;
+    }
+    if (inner && !(i == 2 && z == g.nz - 1)) {
+      const int q0 = z & 3, qm = (z - 1) & 3, qp = (z + 1) & 3;
+      const int rr0 = r + 1;
+      const int xp = ix + 1 == NX ? 0 : ix + 1, xm = ix == 0 ? NX - 1 : ix - 1;
+      const int64_t s = (int64_t)z * g.nxy + t;
+      float E0[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) E0[c] = a.E[(int64_t)(i * 8 + c) * g.V + s];
+      auto nb = [&](int d, int sgn, int& q, int& rr, int& cx) {
+        q = q0;
+        rr = rr0;
+        cx = ix;
+        if (d == 0) cx = sgn > 0 ? xp : xm;
+        else if (d == 1) rr = rr0 + sgn;
+        else q = sgn > 0 ? qp : qm;
+      };
+      G::Sum S = G::zero_sum();
+      const float wt = a.w[0], wz = a.w[2];
+#pragma unroll 1
+      for (int j = 0; j < 3; ++j) {
+        if (j == i) continue;
+        const float wj = j == 2 ? wz : wt;
+        const bool fwd = (j != 2) || (z <= g.nz - 2);
+        const bool bwd = (j != 2) || (z >= 1);
+        int qi, ri, ci, qj, rj, cj_, qn, rn, cn;
+        nb(i, +1, qi, ri, ci);
+        nb(j, +1, qj, rj, cj_);
+        nb(j, -1, qn, rn, cn);
+        if (fwd) {
+          M T = G::mul_d(st_load<RB>(sm, qi, j, ri, ci), st_load<RB>(sm, qj, i, rj, cj_));
+          T = G::mul_d(T, st_load<RB>(sm, q0, j, rr0, ix));
+          G::sum_add(S, wj, T);
+        }
+        if (bwd) {
+          const int qd = i == 2 ? qp : qn, rd = rn + ri - rr0, cd = i == 0 ? ci : cn;
+          M T = G::mul(st_load<RB>(sm, qn, i, rn, cn), st_load<RB>(sm, qd, j, rd, cd));
+          T = G::d_mul(T, st_load<RB>(sm, qn, j, rn, cn));
+          G::sum_add(S, wj, T);
+        }
+      }
+      float pr[8], F[8];
+      const M Ui = st_load<RB>(sm, q0, i, rr0, ix);
+      G::proj_mul_sum(Ui, S, pr);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) F[c] = -pr[c];
+      update_link_ue<3, float>(a, i, t, z, s, F, Ui, E0);
+    }
+    // iteration z is the last to read slice z - 1
+    if (z - 1 >= lo_load) mbar_arrive(&empty[(z - 1) & (kStSlots - 1)]);
+  }
+  if (!good) {
+    abort_flag = 1;
     atomicExch(sa.status, 1);
   }
 }
