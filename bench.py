@@ -114,12 +114,13 @@ def step_kernel_hash():
     return h.hexdigest()[:16]
 
 
-def step_kernel_name(nc, precision, kernel):
+def step_kernel_name(nc, precision, kernel, nx=64):
     """The CUDA kernel glasma_step launches for this choice (the library's
-    automatic choice: plaquette kernel in FP64, one-site staple kernel in
-    FP32)."""
+    automatic choice: plaquette kernel in FP64; in FP32 the staged staple
+    kernel for SU(3) rows of 64 sites, else the one-site staple kernel)."""
     if kernel == "auto":
-        kernel = "plaquette" if precision == "fp64" else "staple"
+        kernel = ("plaquette" if precision == "fp64" else
+                  "staple_staged" if (nc == 3 and nx == 64) else "staple")
     return {"staple": "k_step_leapfrog", "staple_pairs": "k_step_pair",
             "staple_staged": "k_step_staged",
             "plaquette": "k_step_plaq", "plaquette_256": "k_step_plaq"}[kernel]
@@ -134,16 +135,19 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def load_profile_entry(workload, precision, nz):
+def load_profile_entry(workload, precision, nz, kernel=None):
     """The committed ncu figures of the step kernel (per-launch DRAM bytes
-    and FFMA count), valid only for the workload's own lattice and if the
-    kernel sources are unchanged since; else None."""
+    and FFMA count), valid only for the workload's own lattice, for the
+    kernel they were taken on (`kernel`, a CUDA kernel name, if given) and
+    if the kernel sources are unchanged since; else None."""
     path = os.path.join(ROOT, "profiles", "step_traffic.json")
     try:
         if nz != gi.CONFIGS[workload]["nz"]:
             return None
         d = json.load(open(path))
         e = d[workload + ":" + precision]
+        if kernel is not None and not e.get("kernel", "").startswith(kernel):
+            return None
         if e["kernel_hash"] == step_kernel_hash():
             return e
     except Exception:
@@ -151,8 +155,8 @@ def load_profile_entry(workload, precision, nz):
     return None
 
 
-def load_traffic(workload, precision, nz):
-    e = load_profile_entry(workload, precision, nz)
+def load_traffic(workload, precision, nz, kernel=None):
+    e = load_profile_entry(workload, precision, nz, kernel)
     return e["dram_bytes_per_launch"] if e else None
 
 
@@ -376,11 +380,12 @@ def run_ours(args, cfg):
     alg = V * bytes_per_site(nc, rs) + (hops / K) * qbytes
     peak, peak_kind = load_peaks()
     achieved = alg / (per_launch_ms * 1e-3) / 1e9
-    prof = load_profile_entry(args.workload, args.precision, cfg["nz"])
+    kname = step_kernel_name(nc, args.precision, args.kernel, cfg["nx"])
+    prof = load_profile_entry(args.workload, args.precision, cfg["nz"], kname)
     traffic = prof["dram_bytes_per_launch"] if prof else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-            "kernel": step_kernel_name(nc, args.precision, args.kernel),
+            "kernel": kname,
             "peak_source": peak_kind,
             "alg_bytes_per_launch": alg}
     if prof and prof.get("ffma_per_launch"):

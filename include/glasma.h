@@ -388,6 +388,8 @@ GLASMA_API int glasma_slab_unpack(glasma_ctx* c, int dir, const void* dev_buf);
  *                              row fits one block (nx <= 320; its 24% fewer
  *                              FMAs win where the FP64 pipe bounds the
  *                              step), else the staple kernel; for FP32 the
+ *                              staged staple kernel where it applies with
+ *                              nx = 64 (SU(3), whole lattices), else the
  *                              staple kernel. */
 enum { GLASMA_KERNEL_AUTO = 0, GLASMA_KERNEL_STAPLE = 1, GLASMA_KERNEL_PLAQUETTE = 2,
        GLASMA_KERNEL_PLAQUETTE_256 = 3, GLASMA_KERNEL_STAPLE_PAIRS = 4, GLASMA_KERNEL_STAPLE_STAGED = 5 };

@@ -130,13 +130,14 @@ static int check_params(const glasma_params* p) {
 
 // The automatic choice, from CUDA-event timings on GB300: in FP64 the
 // plaquette kernel (24% fewer FMAs, and the FP64 pipe bounds the step:
-// 12.8 against 15.3 ms per SU(3) 512 x 64^2 step); in FP32 SU(3) the
-// one-site staple kernel (0.469 ms, against 0.521 for the plaquette kernel,
-// 0.572 for site pairs, whose 168 registers leave too few warps to hide
-// latency, and 0.47-0.49 for the staged staple kernel, bitwise the same
-// result); in FP32 SU(2) the staple kernel too (1.10 against 1.39 ms for
-// site pairs per 1024 x 128^2 step, once a link's alpha and beta became one
-// 16-byte load: the pairs' 32-bit loads then stride 16 bytes).
+// 12.8 against 15.3 ms per SU(3) 512 x 64^2 step); in FP32 SU(3) with rows
+// of 64 sites the staged staple kernel (0.446-0.449 ms against 0.472-0.475
+// for the one-site staple kernel, bitwise the same result), else the staple
+// kernel (0.469 ms, against 0.521 for the plaquette kernel and 0.572 for
+// site pairs, whose 168 registers leave too few warps to hide latency); in
+// FP32 SU(2) the staple kernel too (1.10 against 1.39 ms for site pairs per
+// 1024 x 128^2 step, once a link's alpha and beta became one 16-byte load:
+// the pairs' 32-bit loads then stride 16 bytes).
 bool use_plaq_kernel(const glasma_ctx* c) {
   if (c->step_kernel == GLASMA_KERNEL_PLAQUETTE || c->step_kernel == GLASMA_KERNEL_PLAQUETTE_256) return plaq_fits(c);
   return c->step_kernel == GLASMA_KERNEL_AUTO && c->rs == 8 && plaq_fits(c);
@@ -148,7 +149,8 @@ bool use_pair_kernel(const glasma_ctx* c) {
 }
 
 bool use_staged_kernel(const glasma_ctx* c) {
-  return c->step_kernel == GLASMA_KERNEL_STAPLE_STAGED && staged_fits(c);
+  if (c->step_kernel == GLASMA_KERNEL_STAPLE_STAGED) return staged_fits(c);
+  return c->step_kernel == GLASMA_KERNEL_AUTO && staged_fits(c) && c->g.nx == 64;
 }
 
 int launch_step_chosen(glasma_ctx* c, bool hop) {

@@ -72,6 +72,10 @@ def test_profile_figures_are_tied_to_the_kernel_sources(monkeypatch):
         assert e["dram_bytes_per_launch"] > 0 and e.get("ffma_per_launch", 1) > 0
     assert bench.load_profile_entry("su3_512x64x64", "fp32", 160) is None
     assert bench.load_profile_entry("su3_512x64x64", "fp64", 512) is None
+    # and only for the kernel they were taken on
+    if e is not None:
+        assert bench.load_profile_entry("su3_512x64x64", "fp32", 512, e["kernel"]) is not None
+        assert bench.load_profile_entry("su3_512x64x64", "fp32", 512, "k_step_plaq") is None
     monkeypatch.setattr(bench, "step_kernel_hash", lambda: "0" * 16)
     assert bench.load_profile_entry("su3_512x64x64", "fp32", 512) is None
     assert bench.load_traffic("su3_512x64x64", "fp32", 512) is None
