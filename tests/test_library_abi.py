@@ -149,3 +149,18 @@ def test_static_residual_rejects_unaligned_links_on_the_host(lib):
                                            0x10008, 0x20000)
         assert e.value.code == "INVALID_ARG"
         assert "16-byte" in str(e.value)
+
+
+def test_kernel_choices_match_the_header():
+    """The binding's kernel names map to the header's GLASMA_KERNEL_* values,
+    and bench.py names the CUDA kernel the automatic choice launches."""
+    import bench
+    from paper_2009_02044_gb300 import glasma as G
+    src = open(os.path.join(ROOT, "include", "glasma.h")).read()
+    enum = dict((k.lower(), int(v)) for k, v in
+                re.findall(r"GLASMA_KERNEL_(\w+)\s*=\s*(\d+)", src))
+    assert enum == G.KERNELS
+    assert bench.step_kernel_name(3, "fp32", "auto", 64) == "k_step_staged"
+    assert bench.step_kernel_name(3, "fp32", "auto", 128) == "k_step_leapfrog"
+    assert bench.step_kernel_name(2, "fp32", "auto", 64) == "k_step_leapfrog"
+    assert bench.step_kernel_name(3, "fp64", "auto", 64) == "k_step_plaq"
