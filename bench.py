@@ -22,7 +22,8 @@ Fields of the JSON line beyond the metric:
                 steps) / its launch time from CUDA events, against the
                 measured HBM copy bandwidth; traffic = DRAM bytes per launch
                 from the committed ncu capture (null once the kernel sources
-                differ from the captured ones); fma_pipe = the FFMA count of
+                differ from the captured ones, or for another kernel than
+                the captured one); fma_pipe = the FFMA count of
                 the same capture over the launch time, against 152 SMs x 128
                 FP32 lanes x the maximum SM clock
   e2e           the same metric through the C ABI from host charges: the
